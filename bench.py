@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Throughput of the ROSAR sparse-aperture imaging path on one GB300 (and N by weak scaling).
+
+Workload (default): the indoor scan, 3600 pulses x 256 ADC samples, K = 64 taps of
+M = 600, 256 x 3600 polar image.  One step = one whole image through the C ABI
+(rosar_image: range compression + sparse azimuth filter).  Metric: image px/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing rules: W warm-up steps, then K timed steps bracketed by barrier +
+synchronize; device time from CUDA events on the launching stream; consecutive
+steps cycle through 16 distinct scan buffers (354 MB, larger than the 129 MB L2),
+so no step finds its inputs in L2.  Under torchrun every rank images its own
+scans (weak scaling, no data-path collective) and rank 0 prints the max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BUF = 16
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the BPA comparison lines")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers --
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("ROSAR_BENCH_GLOO") is None else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2309_08038_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this exact kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                p = line.split()
+                if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload and p[2] == src_hash:
+                    return float(p[3])
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------- workloads --
+
+def indoor_inputs(torch, device, rank):
+    import numpy as np
+    import synth
+    cfg = synth.INDOOR
+    sc = synth.make_scene(cfg)
+    o = synth.draw_offsets(cfg)
+    w = synth.default_weights(cfg, o)
+    win = synth.hann_window(cfg.L)
+    raws = []
+    for b in range(N_BUF):
+        # distinct scans: the same scene seen from a rotated start angle (a circular shift of the pulses)
+        raws.append(torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, 211 * b + 17 * rank, axis=0))).to(device))
+    return cfg, sc, raws, torch.from_numpy(w).to(device), torch.from_numpy(o).to(device), \
+        torch.from_numpy(win).to(device)
+
+
+def time_loop(torch, fn, steps, warmup, stream, world, device):
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(ms, world, device), wall
+
+
+# ------------------------------------------------------------ cpu baseline --
+
+CPU_MIN_SECONDS = 10.0
+
+
+def cpu_baseline_run(min_seconds=CPU_MIN_SECONDS, max_images=50):
+    """Oracle (FP64 numpy) on the indoor workload: whole 256 x 3600 images (range DFT of every
+    pulse + sparse azimuth filter), repeated until `min_seconds` have elapsed.  Returns
+    (px/s, seconds, images)."""
+    import numpy as np
+    import oracle as O
+    import synth
+    cfg = synth.INDOOR
+    rng = np.random.default_rng(5)
+    raw = (rng.standard_normal((cfg.n_az, cfg.L)) + 1j * rng.standard_normal((cfg.n_az, cfg.L))).astype(np.complex64)
+    o = synth.draw_offsets(cfg)
+    w = synth.default_weights(cfg, o)
+    win = synth.hann_window(cfg.L)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_images and (n == 0 or time.perf_counter() - t0 < min_seconds):
+        O.sparse_azimuth(O.range_compress(raw, win), w, o)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n * cfg.L * cfg.n_az / dt, dt, n
+
+
+def cpu_baseline_subprocess(min_seconds=CPU_MIN_SECONDS):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; v, dt, n = bench.cpu_baseline_run(%r); "
+            "print(json.dumps({'v': v, 'dt': dt, 'n': n}))" % (ROOT, float(min_seconds)))
+    res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if res.returncode != 0:
+        return None
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": d["v"], "unit": "px/s", "cores": 1, "kind": "oracle",
+            "sample": f"indoor workload, {d['n']} whole 256x3600 images (range DFT of all 3600 pulses + "
+                      f"sparse azimuth filter), FP64 numpy on one core, {d['dt']:.1f} s"}
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, each step one bounded sample (>= 10 s of whole indoor images);
+    the number of steps is capped so the run ends within a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    steps = max(1, min(args.steps, 3))
+    warm = 1 if args.warmup > 0 else 0
+    vals = []
+    cb = None
+    for i in range(warm + steps):
+        cb = cpu_baseline_subprocess()
+        if cb is None:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's CPU run failed"}))
+            return
+        if i >= warm:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    out = {"impl": "reference", "metric": "image px/s (indoor 3600x256 scan, K=64 of M=600)", "value": v,
+           "unit": "px/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+           "ms_per_step": 256 * 3600 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "indoor scan: 3600 pulses x 256 ADC samples, K=64 of M=600, "
+                                  "256x3600 polar image, complex64",
+                      "steps_note": f"steps capped at {steps} (each >= {CPU_MIN_SECONDS:.0f} s of oracle work)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2309_08038_gb300 as rosar
+    rosar.load()
+    stream = torch.cuda.current_stream()
+
+    cfg, sc, raws, w, o, win = indoor_inputs(torch, device, rank)
+    px = cfg.L * cfg.n_az
+    S_bufs = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(N_BUF)]
+    outs = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(N_BUF)]
+    assert N_BUF * 3 * px * 8 > 2 * L2_BYTES
+
+    def step(i):
+        b = i % N_BUF
+        rosar.image(raws[b], win, w, o, workspace=S_bufs[b], out=outs[b])
+
+    peaks, peak_src = measured_peaks()
+    with ClockSampler(local) as clk:
+        ms, wall = time_loop(torch, step, args.steps, args.warmup, stream, world, device)
+    ms_step = ms / args.steps
+    value = world * px / (ms_step * 1e-3)
+
+    # per-kernel device time, same buffers and launch configuration
+    def k1(i):
+        b = i % N_BUF
+        rosar.range_compress(raws[b], win, out=S_bufs[b])
+
+    def k2(i):
+        b = i % N_BUF
+        rosar.sparse_azimuth(S_bufs[b], w, o, out=outs[b])
+
+    n_k = max(200, args.steps // 4)
+    ms_k1, _ = time_loop(torch, k1, n_k, 5, stream, world, device)
+    ms_k2, _ = time_loop(torch, k2, n_k, 5, stream, world, device)
+    t_k1, t_k2 = ms_k1 / n_k * 1e-3, ms_k2 / n_k * 1e-3
+
+    # algorithmic work per launch
+    K = cfg.K
+    k2_flops = 8.0 * K * px
+    k2_bytes = 16.0 * px + 8.0 * cfg.L * K + 4.0 * K
+    k1_bytes = 16.0 * px
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s, FFMA at max SM clock
+    hbm = float(peaks["hbm_gbs"])
+    k2_tflops = k2_flops / t_k2 / 1e12
+    src = source_hash("sparse_azimuth.cu")
+    roofline = {"kernel": "sparse_azimuth_kernel", "bound": "alu", "achieved": k2_tflops, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": k2_tflops / fp32_peak,
+                "traffic": recorded_traffic("sparse_azimuth_kernel", "indoor", src),
+                "peak_note": f"FP32 FFMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                             f"(sm_max_mhz of {peak_src} peaks)",
+                "algorithmic_flops": k2_flops, "algorithmic_bytes": k2_bytes, "us_per_launch": t_k2 * 1e6,
+                "hbm_gbs": k2_bytes / t_k2 / 1e9, "hbm_frac": k2_bytes / t_k2 / 1e9 / hbm,
+                "hbm_peak_gbs": hbm}
+    kernels = {
+        "range_compress_kernel<256>": {"us_per_launch": t_k1 * 1e6, "algorithmic_bytes": k1_bytes,
+                                       "gbs": k1_bytes / t_k1 / 1e9, "hbm_frac": k1_bytes / t_k1 / 1e9 / hbm,
+                                       "traffic": recorded_traffic("range_compress_kernel<256>", "indoor",
+                                                                   source_hash("range_compress.cu"))},
+        "sparse_azimuth_kernel": {"us_per_launch": t_k2 * 1e6, "tflops": k2_tflops,
+                                  "gbs": k2_bytes / t_k2 / 1e9},
+    }
+
+    # end to end through the public API with pinned host buffers
+    hraw = [r.cpu().pin_memory() for r in raws[:4]]
+    hout = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64).pin_memory() for _ in range(4)]
+
+    def e2e_step(i):
+        b = i % 4
+        raws[b].copy_(hraw[b], non_blocking=True)
+        rosar.image(raws[b], win, w, o, workspace=S_bufs[b], out=outs[b])
+        hout[b].copy_(outs[b], non_blocking=True)
+
+    n_e = max(100, args.steps // 8)
+    ms_e, _ = time_loop(torch, e2e_step, n_e, 5, stream, world, device)
+    e2e = {"value": world * px / (ms_e / n_e * 1e-3), "unit": "px/s", "h2d_bytes_per_step": px * 8,
+           "d2h_bytes_per_step": px * 8, "note": "pinned host raw cube in, image out; weights/offsets/window resident"}
+
+    compare = {}
+    if not args.no_compare:
+        import numpy as np
+        r = cfg.radar
+        radar = rosar.Radar(r.fc, r.slope, r.t_sample(cfg.L), r.t_start, r.r0, r.c)
+        dphi = torch.from_numpy(sc.dphi.astype(np.float32)).to(device)
+        dr = torch.from_numpy(sc.dr.astype(np.float32)).to(device)
+        bo = torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
+
+        def bpa_j(i):
+            rosar.bpa(S_bufs[i % N_BUF], radar, cfg.L, cfg.M_ap, dphi=dphi, dr=dr, out=bo)
+
+        def bpa_n(i):
+            rosar.bpa(S_bufs[i % N_BUF], radar, cfg.L, cfg.M_ap, out=bo)
+
+        ms_bj, _ = time_loop(torch, bpa_j, 20, 2, stream, world, device)
+        ms_bn, _ = time_loop(torch, bpa_n, 20, 2, stream, world, device)
+        t_bj = ms_bj / 20 * 1e-3 + t_k1
+        t_bn = ms_bn / 20 * 1e-3 + t_k1
+        compare = {
+            "fft_bpa_px_s": world * px / t_bj,
+            "fft_bpa_nominal_px_s": world * px / t_bn,
+            "sas_vs_fft_bpa_speedup": t_bj / (ms_step * 1e-3),
+            "sas_time_reduction_vs_fft_bpa": 1.0 - (ms_step * 1e-3) / t_bj,
+            "note": "FFT+BPA = range compression + back-projection over the same M=600 pulses with the "
+                    "supplied rotation errors (per pixel-pulse geometry); nominal = no errors supplied",
+        }
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess()
+
+    if rank == 0:
+        out = {
+            "metric": "image px/s (indoor 3600x256 scan, K=64 of M=600)",
+            "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "indoor scan: 3600 pulses x 256 ADC samples, K=64 of M=600, "
+                                   "256x3600 polar image, complex64",
+                       "step": "rosar_image = range compression + sparse azimuth filter, one scan",
+                       "l2": f"inputs larger than L2: {N_BUF} rotating scan buffers "
+                             f"({N_BUF * 3 * px * 8 / 2**20:.0f} MiB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "clocks": clk.summary(),
+            "gpu_launches": 2 * args.steps,
+            "roofline": roofline,
+            "kernels": kernels,
+            "e2e": e2e,
+            "compare": compare,
+            "cpu_baseline": cpu,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

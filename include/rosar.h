@@ -1,0 +1,147 @@
+/*
+ * rosar.h -- C ABI of librosar, the GB300 (sm_103a) imaging path for rotating
+ * synthetic aperture radar by sparse-aperture azimuth filtering
+ * (arXiv 2309.08038, "Efficient Rotating Synthetic Aperture Radar Imaging via
+ * Robust Sparse Array Synthesis").
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller (cudaMalloc'd or
+ *    torch CUDA tensors, contiguous, at least 8-byte aligned).  Structs passed
+ *    by pointer (rosar_radar, rosar_scan) are HOST pointers read during the call.
+ *  - Complex data is interleaved (re, im) float32: rosar_c32, the layout of
+ *    torch.complex64 and cuFloatComplex.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously; no entry point synchronises the device.
+ *  - Argument errors are detected on the host, before any launch, and return
+ *    ROSAR_ERR_INVALID_ARG / ROSAR_ERR_UNSUPPORTED.  A failed launch returns
+ *    ROSAR_ERR_CUDA.  rosar_last_error() then holds a one-line explanation
+ *    (per host thread).  Nothing here aborts, exits or traps, and no entry point
+ *    allocates device memory: scratch space is passed in by the caller.
+ *  - Sizes are int; every product of sizes must stay below 2^31 elements.
+ *
+ * Notation: n_az = pulses (phase centres) per rotation, the paper's N (Sec. II-A,
+ * Eq. (1)); L = ADC samples per pulse = FFT length = range bins (the paper's M and
+ * L, Sec. III-D); K = sparse taps; M_ap = dense aperture length in pulses.
+ */
+#ifndef ROSAR_H
+#define ROSAR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ROSAR_API __attribute__((visibility("default")))
+#else
+#define ROSAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rosar_c32 {
+    float re, im;
+} rosar_c32;
+
+typedef enum rosar_status {
+    ROSAR_OK = 0,
+    ROSAR_ERR_INVALID_ARG = 1,  /* null pointer, non-positive or inconsistent size */
+    ROSAR_ERR_UNSUPPORTED = 2,  /* valid request outside this build's limits (e.g. L not 2^p in [8, 4096]) */
+    ROSAR_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed; see rosar_last_error() */
+    ROSAR_ERR_TIMEOUT = 4       /* a bounded device-side wait gave up (batched form) */
+} rosar_status;
+
+/* FMCW radar on a rotating arm (Sec. II-A/B; Table "Parameters of the ROSAR System"). */
+typedef struct rosar_radar {
+    double fc_hz;           /* carrier frequency at the start of the ramp, fc (Eq. (6)) */
+    double slope_hz_per_s;  /* chirp slope, the paper's K (Eq. (6)) */
+    double t_sample_s;      /* ADC sampling interval t_s (Eq. (10)) */
+    double t_start_s;       /* ramp start to first ADC sample, T_Start (Eq. (10)) */
+    double r0_m;            /* rotation radius r (Sec. II-A) */
+    double c_mps;           /* propagation speed; 0 selects 299792458 m/s */
+} rosar_radar;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+ROSAR_API const char *rosar_status_string(rosar_status status);
+
+/* Detail of the most recent failure on the calling host thread ("" if none). */
+ROSAR_API const char *rosar_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+ROSAR_API int rosar_version(void);
+
+/*
+ * Range compression of every pulse (Sec. III-D, Eq. (38)):
+ *   S[l][n] = c_l * sum_{m<L} win[m] * raw[n][m] * exp(-j*2*pi*l*m/L),
+ *   c_l = exp(+j*pi*l*(L-1)/L) if centred, else 1.
+ * The centred form takes the DFT about the centre of the ADC window, so a
+ * point target's peak carries the phase 2*k_mid*R_n with
+ * k_mid = 2*pi*(fc + K*(T_Start + t_s*(L-1)/2))/c; centred = 0 is Eq. (38) verbatim.
+ *   raw  [n_az][L] complex, pulse-major (fast time contiguous)         (in)
+ *   win  [L] float window (e.g. symmetric Hann); NULL = rectangular    (in)
+ *   S    [L][n_az] complex, range-major (azimuth contiguous)           (out)
+ * Limits: n_az >= 1; L a power of two in [8, 4096].  raw and S must not overlap.
+ */
+ROSAR_API rosar_status rosar_range_compress(const rosar_c32 *raw, const float *win, int n_az, int L,
+                                  int centred, rosar_c32 *S, void *stream);
+
+/*
+ * Sparse-aperture azimuth matched filter, the FFT+SAS image of Sec. III-D,
+ * Eq. (43) and Algorithm 2, with every tap of row r reading range bin r:
+ *   out[r][theta] = sum_{k<K} w[r][k] * S[r][(theta + o[r][k]) mod n_az]
+ * (w is the conjugate of the paper's weight, which Eq. (43) applies as w^H y).
+ * Taps are accumulated in float32 in increasing k.
+ *   S    [n_rng][n_az] complex, range-major                             (in)
+ *   w    [n_rng][K] complex weights, one vector per range row            (in)
+ *   o    int32 pulse offsets: [K] shared by all rows if o_row_stride == 0,
+ *        else row r uses o[r*o_row_stride + k] (o_row_stride >= K).  Any
+ *        int32 value is valid; the modulo is non-negative.                (in)
+ *   out  [n_rng][n_az] complex image on the polar grid                  (out)
+ * Limits: n_rng, n_az, K >= 1.  out must not overlap S, w or o.
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth(const rosar_c32 *S, const rosar_c32 *w, const int32_t *o,
+                                  int o_row_stride, int n_rng, int n_az, int K,
+                                  rosar_c32 *out, void *stream);
+
+/*
+ * Range-compressed back-projection, the "FFT+BPA" comparison path (Sec. III-D after
+ * Eq. (43), with w_BP = alpha_n exp(-j2kR_n); Eq. (14) with fast time summed by the FFT):
+ *   out[r][theta] = sum_{d=-M_ap/2}^{M_ap-M_ap/2-1} alpha_n * exp(-j*2*k_mid*R_n) * S(R_n/dR, n),
+ *   n = (theta + d) mod n_az,
+ * for the pixel at distance R_r = r0 + r*dR from the rotation centre and angle
+ * 2*pi*theta/n_az, dR = c/(2*K*t_s*L).  R_n is the distance from phase centre n
+ * at radius r0 + pulse_dr[n] and angle 2*pi*n/n_az + pulse_dphi[n] (Eqs. (2), (37));
+ * alpha_n = max(0, cos of the off-bore-sight angle) (Eqs. (3), (8), (15)), 1 when
+ * R_n = 0.  S(x, n) is linear interpolation between bins floor(x) and floor(x)+1
+ * (interp = 1) or the nearest bin floor(x + 0.5) (interp = 0, the paper's l*_n of
+ * Eq. (40)); bins outside 0..L-1 read zero.  S must be the centred range compression.
+ *   S           [L][n_az] complex                                         (in)
+ *   radar       host pointer                                              (in)
+ *   pulse_dphi  [n_az] float angle errors in radians, or NULL (all zero)  (in)
+ *   pulse_dr    [n_az] float radius errors in metres, or NULL (all zero)  (in)
+ *   out         [n_rng][n_az] complex, rows 0..n_rng-1                    (out)
+ * Limits: 1 <= n_rng <= L; 1 <= M_ap <= n_az; L >= 2.
+ */
+ROSAR_API rosar_status rosar_bpa(const rosar_c32 *S, const rosar_radar *radar, const float *pulse_dphi,
+                       const float *pulse_dr, int L, int n_rng, int n_az, int M_ap, int interp,
+                       rosar_c32 *out, void *stream);
+
+/*
+ * Whole FFT+SAS image of one scan (Sec. III-D; Algorithm 2 with the range FFT):
+ * rosar_range_compress(raw, win, centred = 1) into `workspace`, then
+ * rosar_sparse_azimuth over all L range rows into `out`.
+ *   raw        [n_az][L] complex                                          (in)
+ *   win        [L] float or NULL                                          (in)
+ *   w, o, o_row_stride: as rosar_sparse_azimuth with n_rng = L           (in)
+ *   workspace  [L][n_az] complex scratch; holds S on return             (scratch)
+ *   out        [L][n_az] complex image                                   (out)
+ */
+ROSAR_API rosar_status rosar_image(const rosar_c32 *raw, const float *win, const rosar_c32 *w,
+                         const int32_t *o, int o_row_stride, int n_az, int L, int K,
+                         rosar_c32 *workspace, rosar_c32 *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROSAR_H */

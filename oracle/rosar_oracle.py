@@ -171,20 +171,22 @@ def dft_matrix(L):
     return np.exp(-2j * math.pi * lm / L)
 
 
-def range_compress(raw, win, centred=True):
+def range_compress(raw, win, centred=True, bins=None):
     """Range compression of every pulse (Sec. III-D, Eq. (38)).
 
     raw: [n_az, L] complex, pulse-major.  Returns S: [L, n_az], range-major, with
     S[l, n] = c_l * sum_m win[m] * raw[n, m] * exp(-j*2*pi*l*m/L),
     c_l = exp(+j*pi*l*(L-1)/L) if centred else 1.
+    ``bins`` (optional) evaluates only those rows l, returning [len(bins), n_az].
     """
     raw = np.asarray(raw, dtype=np.complex128)
     n_az, L = raw.shape
-    win = np.asarray(win, dtype=np.float64)
-    Y = (raw * win[None, :]) @ dft_matrix(L).T          # [n_az, L]: Y[n, l]
+    win = np.ones(L) if win is None else np.asarray(win, dtype=np.float64)
+    l = np.arange(L) if bins is None else np.asarray(bins, dtype=np.int64)
+    F = np.exp(-2j * math.pi * (np.outer(l, np.arange(L)) % L) / L)     # rows l of the DFT matrix
+    Y = (raw * win[None, :]) @ F.T                      # [n_az, len(l)]: Y[n, l]
     if centred:
-        l = np.arange(L, dtype=np.float64)
-        Y = Y * np.exp(1j * math.pi * l * (L - 1) / L)[None, :]
+        Y = Y * np.exp(1j * math.pi * l.astype(np.float64) * (L - 1) / L)[None, :]
     return np.ascontiguousarray(Y.T)
 
 

@@ -1,0 +1,11 @@
+"""GB300-native ROSAR imaging by sparse-aperture azimuth filtering (arXiv 2309.08038).
+
+The compute path is librosar.so (hand-written CUDA for sm_103a, C ABI declared in
+include/rosar.h); this package is its thin Python binding.  Build it with
+``python -m paper_2309_08038_gb300.build``.
+"""
+
+from ._lib import LIB_PATH, RosarError, load  # noqa: F401
+from .ops import Radar, bpa, image, range_compress, sparse_azimuth  # noqa: F401
+
+__version__ = "0.1.0"

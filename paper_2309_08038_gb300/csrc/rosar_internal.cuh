@@ -1,0 +1,69 @@
+// Internal helpers shared by the librosar translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rosar.h"
+
+namespace rosar {
+
+// Records a one-line error message for rosar_last_error() and returns `st`.
+rosar_status set_error(rosar_status st, const char *fmt, ...);
+
+// Clears the message (called at entry of every API function).
+void clear_error();
+
+// Maps the launch status of the calling thread to ROSAR_OK / ROSAR_ERR_CUDA.
+rosar_status check_launch(const char *what);
+
+static inline bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device.
+// `done` is a per-kernel bit mask of devices already configured.
+rosar_status ensure_smem(const void *func, size_t bytes, unsigned long long *done, const char *what);
+
+// ------------------------------------------------------------ complex ops --
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// acc += a * b, in the order re: a.x*b.x - a.y*b.y, im: a.x*b.y + a.y*b.x
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Non-negative modulo for any int32 value and n >= 1.
+__device__ __forceinline__ int pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------- launchers --
+// Each .cu file exposes a host-side launcher; the API layer validates first.
+
+rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az, int L, int centred,
+                                   float2 *S, cudaStream_t s);
+
+rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
+                                   int n_rng, int n_az, int K, float2 *out, cudaStream_t s);
+
+struct BpaParams {
+    float inv_dR;        // 1/dR, bins per metre
+    float two_f_over_c;  // 2*f_mid/c, cycles of two-way phase per metre
+    double two_f_over_c_d;
+    double dR;
+    double r0;
+};
+
+rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, const float *dr, int L, int n_rng,
+                        int n_az, int M_ap, int interp, float2 *out, cudaStream_t s);
+
+}  // namespace rosar

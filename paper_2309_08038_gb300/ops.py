@@ -1,0 +1,119 @@
+"""Python entry points with the C ABI's names (rosar_range_compress -> range_compress, ...).
+
+Each function validates tensor metadata, allocates outputs with torch when none
+are given, and calls one C-ABI entry point; all arithmetic is in librosar's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import check, ptr, require, stream_handle
+
+C_LIGHT = 299792458.0
+
+
+@dataclass(frozen=True)
+class Radar:
+    """FMCW radar on a rotating arm (mirrors the C struct rosar_radar)."""
+
+    fc_hz: float
+    slope_hz_per_s: float
+    t_sample_s: float
+    t_start_s: float
+    r0_m: float
+    c_mps: float = C_LIGHT
+
+    def as_struct(self) -> _lib.RadarStruct:
+        return _lib.RadarStruct(self.fc_hz, self.slope_hz_per_s, self.t_sample_s, self.t_start_s, self.r0_m,
+                                self.c_mps)
+
+    def bin_spacing(self, L: int) -> float:
+        return self.c_mps / (2.0 * self.slope_hz_per_s * self.t_sample_s * L)
+
+
+def range_compress(raw, win=None, centred=True, out=None, stream=None):
+    """rosar_range_compress: raw [n_az, L] complex64 -> S [L, n_az] complex64 (range-major)."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(L, n_az))
+    check(lib.rosar_range_compress(ptr(raw), ptr(win), n_az, L, int(bool(centred)), ptr(out), stream_handle(stream)))
+    return out
+
+
+def _offsets(o, n_rng, K):
+    require(o, torch.int32, "o")
+    if o.dim() == 1:
+        if o.shape[0] != K:
+            raise ValueError(f"shared offsets must have shape ({K},), got {tuple(o.shape)}")
+        return 0
+    if o.dim() == 2 and o.shape == (n_rng, K):
+        return K
+    raise ValueError(f"offsets must be [K] or [n_rng, K], got {tuple(o.shape)}")
+
+
+def sparse_azimuth(S, w, o, out=None, stream=None):
+    """rosar_sparse_azimuth: out[r, t] = sum_k w[r, k] * S[r, (t + o_k) mod n_az]."""
+    lib = _lib.load()
+    require(S, torch.complex64, "S", ndim=2)
+    n_rng, n_az = S.shape
+    require(w, torch.complex64, "w", ndim=2)
+    if w.shape[0] != n_rng:
+        raise ValueError(f"w must have {n_rng} rows, got {tuple(w.shape)}")
+    K = w.shape[1]
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=S.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    check(lib.rosar_sparse_azimuth(ptr(S), ptr(w), ptr(o), stride, n_rng, n_az, K, ptr(out), stream_handle(stream)))
+    return out
+
+
+def bpa(S, radar: Radar, n_rng, M_ap, interp="linear", dphi=None, dr=None, out=None, stream=None):
+    """rosar_bpa: back-projection of the centred range-compressed S [L, n_az] onto rows 0..n_rng-1."""
+    lib = _lib.load()
+    require(S, torch.complex64, "S", ndim=2)
+    L, n_az = S.shape
+    if dphi is not None:
+        require(dphi, torch.float32, "dphi", shape=(n_az,))
+    if dr is not None:
+        require(dr, torch.float32, "dr", shape=(n_az,))
+    if interp not in ("linear", "nearest"):
+        raise ValueError("interp must be 'linear' or 'nearest'")
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=S.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    st = radar.as_struct()
+    check(lib.rosar_bpa(ptr(S), ctypes.byref(st), ptr(dphi), ptr(dr), L, n_rng, n_az, M_ap,
+                        1 if interp == "linear" else 0, ptr(out), stream_handle(stream)))
+    return out
+
+
+def image(raw, win, w, o, workspace=None, out=None, stream=None):
+    """rosar_image: range compression into `workspace`, then the sparse azimuth filter into `out`."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(w, torch.complex64, "w", shape=(L, w.shape[1]) if w.dim() == 2 else None)
+    K = w.shape[1]
+    stride = _offsets(o, L, K)
+    if workspace is None:
+        workspace = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    require(workspace, torch.complex64, "workspace", shape=(L, n_az))
+    require(out, torch.complex64, "out", shape=(L, n_az))
+    check(lib.rosar_image(ptr(raw), ptr(win), ptr(w), ptr(o), stride, n_az, L, K, ptr(workspace), ptr(out),
+                          stream_handle(stream)))
+    return out

@@ -1,0 +1,95 @@
+"""The C ABI: librosar.so loads, exports every function include/*.h declares, and rejects
+bad arguments on the host before any launch (CPU only; no compute call is made)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2309_08038_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(rosar_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("rosar_range_compress", "rosar_sparse_azimuth", "rosar_bpa", "rosar_image",
+                 "rosar_status_string", "rosar_last_error"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.rosar_status_string(0) == b"ROSAR_OK"
+    assert lib.rosar_status_string(2) == b"ROSAR_ERR_UNSUPPORTED"
+    assert lib.rosar_status_string(99) == b"ROSAR_ERR_UNKNOWN"
+    assert lib.rosar_version() >= 100
+
+
+FAKE = ctypes.c_void_p(0x10000)      # never dereferenced: validation fails first
+FAKE2 = ctypes.c_void_p(0x20000000)
+
+
+def test_range_compress_rejects_bad_arguments(lib):
+    assert lib.rosar_range_compress(None, None, 10, 64, 1, FAKE2, None) == 1
+    assert lib.rosar_range_compress(FAKE, None, 0, 64, 1, FAKE2, None) == 1
+    assert lib.rosar_range_compress(FAKE, None, 10, 48, 1, FAKE2, None) == 2
+    assert b"power of two" in lib.rosar_last_error()
+    assert lib.rosar_range_compress(FAKE, None, 10, 8192, 1, FAKE2, None) == 2
+    assert lib.rosar_range_compress(FAKE, None, 10, 64, 1, FAKE, None) == 1          # in place
+    assert lib.rosar_range_compress(ctypes.c_void_p(0x10004), None, 10, 64, 1, FAKE2, None) == 1   # misaligned
+
+
+def test_sparse_azimuth_rejects_bad_arguments(lib):
+    f = lib.rosar_sparse_azimuth
+    assert f(FAKE, FAKE, None, 0, 4, 100, 8, FAKE2, None) == 1
+    assert f(FAKE, FAKE, FAKE, 0, 4, 100, 0, FAKE2, None) == 1
+    assert f(FAKE, FAKE, FAKE, 5, 4, 100, 8, FAKE2, None) == 1          # row stride < K
+    assert b"o_row_stride" in lib.rosar_last_error()
+    assert f(FAKE, FAKE, FAKE, 0, 4, 100, 8, FAKE, None) == 1           # out aliases S
+
+
+def test_bpa_rejects_bad_arguments(lib):
+    from paper_2309_08038_gb300 import _lib as L
+    rad = L.RadarStruct(77e9, 1e14, 1e-7, 8e-6, 0.25, 0.0)
+    f = lib.rosar_bpa
+    assert f(FAKE, ctypes.byref(rad), None, None, 64, 65, 360, 60, 1, FAKE2, None) == 1      # n_rng > L
+    assert f(FAKE, ctypes.byref(rad), None, None, 64, 64, 360, 361, 1, FAKE2, None) == 1     # M_ap > n_az
+    assert f(FAKE, ctypes.byref(rad), None, None, 64, 64, 360, 60, 2, FAKE2, None) == 1      # interp
+    bad = L.RadarStruct(77e9, 0.0, 1e-7, 8e-6, 0.25, 0.0)
+    assert f(FAKE, ctypes.byref(bad), None, None, 64, 64, 360, 60, 1, FAKE2, None) == 1
+    assert f(FAKE, None, None, None, 64, 64, 360, 60, 1, FAKE2, None) == 1
+
+
+def test_image_rejects_bad_arguments(lib):
+    f = lib.rosar_image
+    assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2
+    assert f(FAKE, None, FAKE, FAKE, 0, 100, 64, 8, None, ctypes.c_void_p(0x40000000), None) == 1
+
+
+def test_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    import paper_2309_08038_gb300 as rosar
+    raw = torch.zeros((8, 64), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="CUDA"):
+        rosar.range_compress(raw)
