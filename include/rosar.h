@@ -140,6 +140,26 @@ ROSAR_API rosar_status rosar_image(const rosar_c32 *raw, const float *win, const
                          const int32_t *o, int o_row_stride, int n_az, int L, int K,
                          rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
+/*
+ * rosar_image without a caller-provided workspace, for callers that cannot
+ * allocate device memory: a plugin whose host passes in device buffers but no
+ * allocator, or a real-time loop that may not call cudaMalloc after start-up
+ * (it can stall the whole device).  The paper has no counterpart; this is a
+ * deployment convenience with the same result as rosar_image.
+ *   raw, win, w, o, o_row_stride, n_az, L, K, out: as rosar_image.
+ * The range-compressed intermediate lives in a fixed array inside the library
+ * (ROSAR_NOALLOC_MAX_ELEMS complex elements = 16 MiB, held on every GPU that
+ * loads the library until the process exits); L*n_az beyond that returns
+ * ROSAR_ERR_UNSUPPORTED.  The first call on each device looks up the array's
+ * device address, so make it before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU race and must be serialised.  Nothing
+ * is allocated, by this library or any library it calls.
+ */
+#define ROSAR_NOALLOC_MAX_ELEMS (1 << 21)
+ROSAR_API rosar_status rosar_image_noalloc(const rosar_c32 *raw, const float *win, const rosar_c32 *w,
+                                           const int32_t *o, int o_row_stride, int n_az, int L, int K,
+                                           rosar_c32 *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,10 @@ _PROTOS = {
     "rosar_sparse_azimuth": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
 }
+
+NOALLOC_MAX_ELEMS = 1 << 21
 
 
 def load(path: str = LIB_PATH):

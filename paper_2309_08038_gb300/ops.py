@@ -117,3 +117,23 @@ def image(raw, win, w, o, workspace=None, out=None, stream=None):
     check(lib.rosar_image(ptr(raw), ptr(win), ptr(w), ptr(o), stride, n_az, L, K, ptr(workspace), ptr(out),
                           stream_handle(stream)))
     return out
+
+
+def image_noalloc(raw, win, w, o, out=None, stream=None):
+    """rosar_image_noalloc: the same image as `image`, for callers that cannot allocate device
+    scratch (the range-compressed intermediate lives in a fixed 16 MiB array inside librosar).
+    L * n_az must not exceed NOALLOC_MAX_ELEMS; concurrent calls on different streams race."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(w, torch.complex64, "w", ndim=2)
+    K = w.shape[1]
+    stride = _offsets(o, L, K)
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(L, n_az))
+    check(lib.rosar_image_noalloc(ptr(raw), ptr(win), ptr(w), ptr(o), stride, n_az, L, K, ptr(out),
+                                  stream_handle(stream)))
+    return out
