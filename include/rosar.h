@@ -27,6 +27,7 @@
 #ifndef ROSAR_H
 #define ROSAR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -139,6 +140,67 @@ ROSAR_API rosar_status rosar_bpa(const rosar_c32 *S, const rosar_radar *radar, c
 ROSAR_API rosar_status rosar_image(const rosar_c32 *raw, const float *win, const rosar_c32 *w,
                          const int32_t *o, int o_row_stride, int n_az, int L, int K,
                          rosar_c32 *workspace, rosar_c32 *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many scans of uneven n_az, L and K imaged by ONE persistent
+ * kernel launch, captured once in a CUDA graph.
+ *
+ * The persistent CTAs pull tiles from an atomic ticket counter: range tiles
+ * (P pulses of one scan through the range FFT, as rosar_range_compress) and
+ * azimuth tiles (one row segment of one scan through the gather-MAC filter, as
+ * rosar_sparse_azimuth).  An azimuth tile waits, on the device, until every range
+ * tile of its scan has completed.  Every range tile of a scan holds a smaller
+ * ticket than any of its azimuth tiles, so the tiles a wait depends on are
+ * already owned by running CTAs and the wait ends; it is nevertheless bounded
+ * (spin_limit polls), after which the kernel records ROSAR_ERR_TIMEOUT and
+ * every CTA returns.  Results equal rosar_image scan by scan.
+ * ------------------------------------------------------------------------ */
+typedef struct rosar_scan {
+    const rosar_c32 *raw;   /* [n_az][L] complex input                                  (in) */
+    const float *win;       /* [L] window or NULL                                       (in) */
+    const rosar_c32 *w;     /* [L][K] weights                                           (in) */
+    const int32_t *o;       /* [K] shared offsets (o_row_stride 0) or rows of o_row_stride (in) */
+    int o_row_stride;
+    int n_az;               /* >= 1 */
+    int L;                  /* power of two in [16, 2048] */
+    int K;                  /* >= 1 */
+    rosar_c32 *S;           /* [L][n_az] workspace: range-compressed data          (scratch) */
+    rosar_c32 *out;         /* [L][n_az] image                                          (out) */
+} rosar_scan;
+
+typedef struct rosar_batch_tuning {
+    int az_tile;            /* azimuth outputs per tile: 256, 512, 1024 or 2048; 0 selects 1024 */
+    int ctas_per_sm;        /* persistent CTAs per SM; 0 or more than fit selects the occupancy limit */
+    int interleave;         /* 0: every range tile first, then every azimuth tile; 1: scan by scan */
+    int spin_limit;         /* polls (~0.1 us apart) before a dependency wait gives up; 0 selects 2^24 */
+    int debug_unmet_scan;   /* test hook, -1 = off: scan whose azimuth tiles wait for one range tile
+                               more than exists, so that their wait must time out */
+} rosar_batch_tuning;
+
+typedef struct rosar_batch rosar_batch;   /* opaque host handle */
+
+/* Device workspace the batch needs for its descriptors and counters. */
+ROSAR_API size_t rosar_batch_workspace_bytes(int n_scans);
+
+/* Validates the scans (host array, read during the call), writes the descriptors into
+ * `workspace` (device, >= rosar_batch_workspace_bytes(n_scans), synchronous copy) and
+ * captures [counter reset, persistent kernel] into a CUDA graph.  `tuning` may be NULL
+ * (defaults).  The scans' buffers are bound at creation: later launches re-read them. */
+ROSAR_API rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosar_batch_tuning *tuning,
+                                          void *workspace, size_t workspace_bytes, rosar_batch **batch);
+
+/* Enqueues the graph (one cudaGraphLaunch) on `stream`. */
+ROSAR_API rosar_status rosar_batch_launch(rosar_batch *batch, void *stream);
+
+/* Waits for `stream`, then reports ROSAR_OK or ROSAR_ERR_TIMEOUT (a dependency wait gave up). */
+ROSAR_API rosar_status rosar_batch_status(rosar_batch *batch, void *stream);
+
+/* Number of tiles (range, azimuth), persistent CTAs and shared bytes per CTA; any pointer may be NULL. */
+ROSAR_API rosar_status rosar_batch_info(const rosar_batch *batch, int *range_tiles, int *azimuth_tiles,
+                                        int *ctas, int *smem_bytes);
+
+/* Releases the graph and the host handle (not the caller's workspace). */
+ROSAR_API rosar_status rosar_batch_destroy(rosar_batch *batch);
 
 /*
  * rosar_image without a caller-provided workspace, for callers that cannot

@@ -30,6 +30,17 @@ class RadarStruct(ctypes.Structure):
                 ("t_start_s", ctypes.c_double), ("r0_m", ctypes.c_double), ("c_mps", ctypes.c_double)]
 
 
+class ScanStruct(ctypes.Structure):
+    _fields_ = [("raw", ctypes.c_void_p), ("win", ctypes.c_void_p), ("w", ctypes.c_void_p), ("o", ctypes.c_void_p),
+                ("o_row_stride", ctypes.c_int), ("n_az", ctypes.c_int), ("L", ctypes.c_int), ("K", ctypes.c_int),
+                ("S", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class BatchTuningStruct(ctypes.Structure):
+    _fields_ = [("az_tile", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("interleave", ctypes.c_int),
+                ("spin_limit", ctypes.c_int), ("debug_unmet_scan", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _PROTOS = {
@@ -41,6 +52,13 @@ _PROTOS = {
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_batch_workspace_bytes": (ctypes.c_size_t, [_I]),
+    "rosar_batch_create": (_I, [ctypes.POINTER(ScanStruct), _I, ctypes.POINTER(BatchTuningStruct), _P,
+                                ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "rosar_batch_launch": (_I, [_P, _P]),
+    "rosar_batch_status": (_I, [_P, _P]),
+    "rosar_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rosar_batch_destroy": (_I, [_P]),
 }
 
 NOALLOC_MAX_ELEMS = 1 << 21

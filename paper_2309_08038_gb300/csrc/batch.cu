@@ -1,0 +1,373 @@
+// Batched form: many uneven scans, one persistent launch inside a CUDA graph.
+//
+// Work is a list of tiles in ticket order.  A range tile runs the range-FFT tile
+// (fft_tile.cuh) on P = 4096/L pulses of one scan with the CTA's 256 threads; an
+// azimuth tile runs the gather-MAC tile (azimuth_tile.cuh) on 256*J outputs of one
+// row of one scan.  Tickets are handed out by an atomic counter, range tiles of a
+// scan always before its azimuth tiles; the scan's done-counter is bumped (release)
+// after each range tile, and an azimuth tile's thread 0 polls it (acquire) before
+// the CTA reads S through L2.  The poll is bounded; on expiry the kernel raises an
+// error word that every CTA checks before taking its next ticket.
+
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "azimuth_tile.cuh"
+#include "fft_tile.cuh"
+
+namespace rosar {
+namespace {
+
+constexpr int BT_THREADS = 256;
+
+struct ScanDev {
+    const float2 *raw;
+    const float *win;
+    const float2 *w;
+    const int32_t *o;
+    float2 *S;
+    float2 *out;
+    int o_row_stride, n_az, L, K;
+    int range_tiles, az_tiles_per_row, P, vec_store;
+};
+
+struct Segment {
+    int first;   // first ticket
+    int scan;
+    int kind;    // 0 range tiles, 1 azimuth tiles
+    int count;
+};
+
+// counters[0] ticket head, [1] error flag, [2] scan that timed out, [3] unused, [4 + s] range tiles done of scan s
+constexpr int CNT_HEAD = 0, CNT_ERR = 1, CNT_ERR_SCAN = 2, CNT_DONE = 4;
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int L>
+__device__ __forceinline__ void run_range(const ScanDev &sc, int n0, char *sm, bool build) {
+    fft::range_tile<L, 4096 / L>(sc.raw, sc.win, sc.n_az, true, sc.S, n0, reinterpret_cast<float2 *>(sm), build,
+                                 sc.vec_store != 0);
+}
+
+template <int J>
+__global__ void __launch_bounds__(BT_THREADS, 3)
+batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs, int n_segs, int total,
+             int *counters, int spin_limit, int debug_scan) {
+    extern __shared__ __align__(16) char sm[];
+    __shared__ int red[2 * az::THREADS / 32];
+    __shared__ int s_ticket, s_abort;
+    int *head = counters + CNT_HEAD, *err = counters + CNT_ERR, *done = counters + CNT_DONE;
+    int tab_L = 0;   // L of the twiddle table left in shared memory by the previous range tile
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = atomicAdd(head, 1);
+            if (t < total && ld_relaxed(err) != 0) t = total;
+            s_ticket = t;
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int t = s_ticket;
+        if (t >= total) break;
+        int lo = 0, hi = n_segs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&segs[mid].first) <= t) lo = mid; else hi = mid - 1;
+        }
+        const Segment sg = segs[lo];
+        const ScanDev sc = scans[sg.scan];
+        const int local = t - sg.first;
+        if (sg.kind == 0) {
+            const bool build = tab_L != sc.L;
+            const int n0 = local * sc.P;
+            switch (sc.L) {
+                case 16: run_range<16>(sc, n0, sm, build); break;
+                case 32: run_range<32>(sc, n0, sm, build); break;
+                case 64: run_range<64>(sc, n0, sm, build); break;
+                case 128: run_range<128>(sc, n0, sm, build); break;
+                case 256: run_range<256>(sc, n0, sm, build); break;
+                case 512: run_range<512>(sc, n0, sm, build); break;
+                case 1024: run_range<1024>(sc, n0, sm, build); break;
+                default: run_range<2048>(sc, n0, sm, build); break;
+            }
+            tab_L = sc.L;
+            __threadfence();       // this thread's S stores are visible device-wide ...
+            __syncthreads();       // ... for every thread of the tile ...
+            if (threadIdx.x == 0) atomicAdd(done + sg.scan, 1);   // ... before the tile is counted
+        } else {
+            tab_L = 0;             // the azimuth tile overwrites the table
+            if (threadIdx.x == 0) {
+                const int need = sc.range_tiles + (sg.scan == debug_scan ? 1 : 0);
+                int polls = 0;
+                while (ld_acquire(done + sg.scan) < need) {
+                    if (++polls > spin_limit || ((polls & 255) == 0 && ld_relaxed(err) != 0)) {
+                        if (atomicExch(err, 1) == 0) atomicExch(counters + CNT_ERR_SCAN, sg.scan);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            const int r = local / sc.az_tiles_per_row;
+            const int th0 = (local - r * sc.az_tiles_per_row) * az::Geo<J>::TW;
+            az::azimuth_tile<J, true>(sc.S, sc.w, sc.o, sc.o_row_stride, sc.n_az, sc.K, sc.out, r, th0, sm, red);
+        }
+    }
+}
+
+using KernelFn = void (*)(const ScanDev *, const Segment *, int, int, int *, int, int);
+
+KernelFn kernel_for(int J) {
+    switch (J) {
+        case 1: return batch_kernel<1>;
+        case 2: return batch_kernel<2>;
+        case 8: return batch_kernel<8>;
+        default: return batch_kernel<4>;
+    }
+}
+
+unsigned long long g_smem_done[4] = {0, 0, 0, 0};
+
+int j_index(int J) { return J == 1 ? 0 : J == 2 ? 1 : J == 4 ? 2 : 3; }
+
+int range_smem_bytes(int L) {
+    switch (L) {
+        case 16: return (int)fft::Tile<16, 256>::SMEM;
+        case 32: return (int)fft::Tile<32, 128>::SMEM;
+        case 64: return (int)fft::Tile<64, 64>::SMEM;
+        case 128: return (int)fft::Tile<128, 32>::SMEM;
+        case 256: return (int)fft::Tile<256, 16>::SMEM;
+        case 512: return (int)fft::Tile<512, 8>::SMEM;
+        case 1024: return (int)fft::Tile<1024, 4>::SMEM;
+        default: return (int)fft::Tile<2048, 2>::SMEM;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace rosar
+
+using namespace rosar;
+
+struct rosar_batch {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int *counters;           // device
+    int n_scans;
+    int range_tiles, az_tiles, ctas, smem;
+};
+
+extern "C" {
+
+size_t rosar_batch_workspace_bytes(int n_scans) {
+    if (n_scans < 1) return 0;
+    return align256(sizeof(ScanDev) * (size_t)n_scans) + align256(sizeof(Segment) * 2 * (size_t)n_scans) +
+           align256(sizeof(int) * (CNT_DONE + (size_t)n_scans));
+}
+
+rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosar_batch_tuning *tuning,
+                                void *workspace, size_t workspace_bytes, rosar_batch **batch) {
+    clear_error();
+    if (!scans || !workspace || !batch) return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: null argument");
+    *batch = nullptr;
+    if (n_scans < 1) return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: n_scans=%d < 1", n_scans);
+    if (workspace_bytes < rosar_batch_workspace_bytes(n_scans))
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: workspace of %zu bytes < %zu needed", workspace_bytes,
+                         rosar_batch_workspace_bytes(n_scans));
+    if (reinterpret_cast<uintptr_t>(workspace) % 256)
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: workspace must be 256-byte aligned");
+    rosar_batch_tuning tn = {1024, 0, 0, 1 << 24, -1};
+    if (tuning) tn = *tuning;
+    if (tn.az_tile == 0) tn.az_tile = 1024;
+    if (tn.spin_limit <= 0) tn.spin_limit = 1 << 24;
+    const int J = tn.az_tile / az::THREADS;
+    if (tn.az_tile % az::THREADS || (J != 1 && J != 2 && J != 4 && J != 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: az_tile=%d not in {256, 512, 1024, 2048}", tn.az_tile);
+
+    ScanDev *hs = static_cast<ScanDev *>(calloc((size_t)n_scans, sizeof(ScanDev)));
+    Segment *hg = static_cast<Segment *>(calloc(2 * (size_t)n_scans, sizeof(Segment)));
+    if (!hs || !hg) {
+        free(hs);
+        free(hg);
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: host allocation failed");
+    }
+    int smem = az::Geo<8>::SMEM_BYTES;
+    switch (J) {
+        case 1: smem = az::Geo<1>::SMEM_BYTES; break;
+        case 2: smem = az::Geo<2>::SMEM_BYTES; break;
+        case 4: smem = az::Geo<4>::SMEM_BYTES; break;
+        default: break;
+    }
+    long long total_range = 0, total_az = 0;
+    rosar_status st = ROSAR_OK;
+    for (int s = 0; s < n_scans && st == ROSAR_OK; ++s) {
+        const rosar_scan &q = scans[s];
+        if (!q.raw || !q.w || !q.o || !q.S || !q.out)
+            st = set_error(ROSAR_ERR_INVALID_ARG, "batch_create: scan %d has a null pointer", s);
+        else if (q.n_az < 1 || q.K < 1 || (q.o_row_stride != 0 && q.o_row_stride < q.K))
+            st = set_error(ROSAR_ERR_INVALID_ARG, "batch_create: scan %d: n_az=%d K=%d o_row_stride=%d", s, q.n_az,
+                           q.K, q.o_row_stride);
+        else if (!is_pow2(q.L) || q.L < 16 || q.L > 2048)
+            st = set_error(ROSAR_ERR_UNSUPPORTED, "batch_create: scan %d: L=%d not a power of two in [16, 2048]", s,
+                           q.L);
+        else if ((long long)q.L * q.n_az > (1LL << 31) - 1)
+            st = set_error(ROSAR_ERR_UNSUPPORTED, "batch_create: scan %d too large", s);
+        if (st != ROSAR_OK) break;
+        ScanDev &d = hs[s];
+        d.raw = reinterpret_cast<const float2 *>(q.raw);
+        d.win = q.win;
+        d.w = reinterpret_cast<const float2 *>(q.w);
+        d.o = q.o;
+        d.S = reinterpret_cast<float2 *>(q.S);
+        d.out = reinterpret_cast<float2 *>(q.out);
+        d.o_row_stride = q.o_row_stride;
+        d.n_az = q.n_az;
+        d.L = q.L;
+        d.K = q.K;
+        d.P = 4096 / q.L;
+        d.range_tiles = (q.n_az + d.P - 1) / d.P;
+        d.az_tiles_per_row = (q.n_az + tn.az_tile - 1) / tn.az_tile;
+        d.vec_store = (q.n_az % 2 == 0) && (reinterpret_cast<uintptr_t>(q.S) % 16 == 0);
+        smem = smem > range_smem_bytes(q.L) ? smem : range_smem_bytes(q.L);
+        total_range += d.range_tiles;
+        total_az += (long long)d.az_tiles_per_row * q.L;
+    }
+    if (st == ROSAR_OK && total_range + total_az > (1LL << 31) - 1)
+        st = set_error(ROSAR_ERR_UNSUPPORTED, "batch_create: %lld tiles exceed 2^31", total_range + total_az);
+    if (st != ROSAR_OK) {
+        free(hs);
+        free(hg);
+        return st;
+    }
+    // ticket order
+    int first = 0, ns = 0;
+    if (tn.interleave) {
+        for (int s = 0; s < n_scans; ++s) {
+            hg[ns++] = {first, s, 0, hs[s].range_tiles};
+            first += hs[s].range_tiles;
+            const int na = hs[s].az_tiles_per_row * hs[s].L;
+            hg[ns++] = {first, s, 1, na};
+            first += na;
+        }
+    } else {
+        for (int s = 0; s < n_scans; ++s) {
+            hg[ns++] = {first, s, 0, hs[s].range_tiles};
+            first += hs[s].range_tiles;
+        }
+        for (int s = 0; s < n_scans; ++s) {
+            const int na = hs[s].az_tiles_per_row * hs[s].L;
+            hg[ns++] = {first, s, 1, na};
+            first += na;
+        }
+    }
+    const int total = first;
+
+    char *ws = static_cast<char *>(workspace);
+    ScanDev *d_scans = reinterpret_cast<ScanDev *>(ws);
+    Segment *d_segs = reinterpret_cast<Segment *>(ws + align256(sizeof(ScanDev) * (size_t)n_scans));
+    int *d_cnt = reinterpret_cast<int *>(ws + align256(sizeof(ScanDev) * (size_t)n_scans) +
+                                         align256(sizeof(Segment) * 2 * (size_t)n_scans));
+    cudaError_t e = cudaMemcpy(d_scans, hs, sizeof(ScanDev) * (size_t)n_scans, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_segs, hg, sizeof(Segment) * (size_t)ns, cudaMemcpyHostToDevice);
+    free(hs);
+    free(hg);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "batch_create: descriptor copy: %s", cudaGetErrorString(e));
+
+    KernelFn fn = kernel_for(J);
+    st = ensure_smem((const void *)fn, (size_t)smem, &g_smem_done[j_index(J)], "batch_create");
+    if (st != ROSAR_OK) return st;
+    int dev = 0, n_sm = 0, occ = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT_THREADS, (size_t)smem);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "batch_create: occupancy query: %s", cudaGetErrorString(e));
+    if (occ < 1) return set_error(ROSAR_ERR_UNSUPPORTED, "batch_create: %d B of shared memory per CTA does not fit", smem);
+    const int per_sm = (tn.ctas_per_sm > 0 && tn.ctas_per_sm < occ) ? tn.ctas_per_sm : occ;
+    int grid = per_sm * n_sm;
+    if (grid > total) grid = total;
+
+    rosar_batch *b = new (std::nothrow) rosar_batch();
+    if (!b) return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: host allocation failed");
+    b->counters = d_cnt;
+    b->n_scans = n_scans;
+    b->range_tiles = (int)total_range;
+    b->az_tiles = (int)total_az;
+    b->ctas = grid;
+    b->smem = smem;
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(d_cnt, 0, sizeof(int) * (CNT_DONE + (size_t)n_scans), cs);
+        fn<<<grid, BT_THREADS, smem, cs>>>(d_scans, d_segs, ns, total, d_cnt, tn.spin_limit, tn.debug_unmet_scan);
+        e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        delete b;
+        return set_error(ROSAR_ERR_CUDA, "batch_create: graph capture: %s", cudaGetErrorString(e));
+    }
+    *batch = b;
+    return ROSAR_OK;
+}
+
+rosar_status rosar_batch_launch(rosar_batch *batch, void *stream) {
+    clear_error();
+    if (!batch) return set_error(ROSAR_ERR_INVALID_ARG, "batch_launch: null batch");
+    const cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "batch_launch: %s", cudaGetErrorString(e));
+    return ROSAR_OK;
+}
+
+rosar_status rosar_batch_status(rosar_batch *batch, void *stream) {
+    clear_error();
+    if (!batch) return set_error(ROSAR_ERR_INVALID_ARG, "batch_status: null batch");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    int flags[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(flags, batch->counters, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "batch_status: %s", cudaGetErrorString(e));
+    if (flags[CNT_ERR])
+        return set_error(ROSAR_ERR_TIMEOUT, "batch: an azimuth tile of scan %d gave up waiting for its range tiles",
+                         flags[CNT_ERR_SCAN]);
+    return ROSAR_OK;
+}
+
+rosar_status rosar_batch_info(const rosar_batch *batch, int *range_tiles, int *azimuth_tiles, int *ctas,
+                              int *smem_bytes) {
+    clear_error();
+    if (!batch) return set_error(ROSAR_ERR_INVALID_ARG, "batch_info: null batch");
+    if (range_tiles) *range_tiles = batch->range_tiles;
+    if (azimuth_tiles) *azimuth_tiles = batch->az_tiles;
+    if (ctas) *ctas = batch->ctas;
+    if (smem_bytes) *smem_bytes = batch->smem;
+    return ROSAR_OK;
+}
+
+rosar_status rosar_batch_destroy(rosar_batch *batch) {
+    clear_error();
+    if (!batch) return ROSAR_OK;
+    cudaError_t e1 = cudaGraphExecDestroy(batch->exec);
+    cudaError_t e2 = cudaGraphDestroy(batch->graph);
+    delete batch;
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return set_error(ROSAR_ERR_CUDA, "batch_destroy: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    return ROSAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Shared-memory radix-16 Stockham FFT tile used by the range-compression kernels
+// (arXiv 2309.08038, Sec. III-D, Eq. (38)): window at load, centring phase
+// c_l = exp(+j*pi*l*(L-1)/L) and the pulse-major -> range-major transpose at store.
+#pragma once
+
+#include "rosar_internal.cuh"
+
+namespace rosar {
+namespace fft {
+
+// exp(-2*pi*i*q/16) for compile-time q (after unrolling the switch folds away).
+__device__ __forceinline__ float2 w16(int q) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    switch (q & 15) {
+        case 0: return make_float2(1.f, 0.f);
+        case 1: return make_float2(c1, -s1);
+        case 2: return make_float2(h, -h);
+        case 3: return make_float2(s1, -c1);
+        case 4: return make_float2(0.f, -1.f);
+        case 5: return make_float2(-s1, -c1);
+        case 6: return make_float2(-h, -h);
+        case 7: return make_float2(-c1, -s1);
+        case 8: return make_float2(-1.f, 0.f);
+        case 9: return make_float2(-c1, s1);
+        case 10: return make_float2(-h, h);
+        case 11: return make_float2(-s1, c1);
+        case 12: return make_float2(0.f, 1.f);
+        case 13: return make_float2(s1, c1);
+        case 14: return make_float2(h, h);
+        default: return make_float2(c1, s1);
+    }
+}
+
+__device__ __forceinline__ float2 twmul16(float2 d, int q) {
+    q &= 15;
+    if (q == 0) return d;
+    if (q == 4) return make_float2(d.y, -d.x);
+    if (q == 8) return make_float2(-d.x, -d.y);
+    if (q == 12) return make_float2(-d.y, d.x);
+    return cmul(d, w16(q));
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+__host__ __device__ constexpr int brev(int x, int bits) {
+    int y = 0;
+    for (int i = 0; i < bits; ++i) y |= ((x >> i) & 1) << (bits - 1 - i);
+    return y;
+}
+
+// In-register radix-2 decimation-in-frequency DFT of size R <= 16 on v[0..R).
+// Output index r ends up in v[brev(r)].
+template <int R>
+__device__ __forceinline__ void dft_dif(float2 *v) {
+    constexpr int LG = ilog2(R);
+#pragma unroll
+    for (int s = 0; s < LG; ++s) {
+        const int span = R >> (s + 1);
+#pragma unroll
+        for (int start = 0; start < R; start += 2 * span) {
+#pragma unroll
+            for (int i = 0; i < span; ++i) {
+                const float2 a = v[start + i], b = v[start + i + span];
+                v[start + i] = cadd(a, b);
+                v[start + i + span] = twmul16(csub(a, b), i * (16 / (2 * span)));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
+// Geometry of a tile of P pulses of length L transformed by T*P threads.
+template <int L, int P_>
+struct Tile {
+    static constexpr int P = P_;
+    static constexpr int RM = L >= 16 ? 16 : L;       // elements per thread
+    static constexpr int T = L / RM;                   // threads per pulse
+    static constexpr int LG = ilog2(L);
+    static constexpr int NF = L >= 16 ? LG / 4 : 0;    // full radix-16 passes
+    static constexpr int RR = L >= 16 ? (L >> (4 * NF)) : 1;   // remainder radix (1 = none)
+    static constexpr int LP = L + L / 16;              // padded per-pulse stride in the FFT buffer
+    static constexpr int TP = P + 2;                   // row stride of the transposed tile (16-B aligned)
+    static constexpr int BUF = (P * LP > L * TP) ? P * LP : L * TP;
+    static constexpr int THREADS = T * P;
+    static constexpr int SMEM_ELEMS = 2 * L + BUF;     // float2 elements: twiddle table + buffer
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)SMEM_ELEMS;
+    static_assert(P % 2 == 0, "pulse tiles hold an even number of pulses");
+};
+
+// One Stockham pass of radix R (sub-transform size NS before the pass).
+// FIRST: v already holds x[t + r*T] (loaded from HBM).  LAST: write the transposed tile.
+template <int L, int P, int R, int NS, bool FIRST, bool LAST>
+__device__ __forceinline__ void stockham_pass(float2 (&v)[Tile<L, P>::RM], int t, int p, float2 *pb, float2 *tile,
+                                              const float2 *tab, bool centred) {
+    using PL = Tile<L, P>;
+    constexpr int RM = PL::RM, T = PL::T, NB = RM / R;
+    if (!FIRST) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + b * T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = pb[pad16(j + r * (L / R))];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * T;
+        const int k = j & (NS - 1);
+        if (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tab[2 * r * k * (L / (NS * R))]);
+        }
+        dft_dif<R>(v + b * R);
+    }
+    __syncthreads();   // every thread has read its inputs from the buffer (or the table is ready)
+    if (!LAST) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + b * T;
+            const int k = j & (NS - 1);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) pb[pad16(base + r * NS)] = v[b * R + brev(r, ilog2(R))];
+        }
+    } else {
+        // last pass: NS*R == L, so j < NS and bin l = j + r*NS
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + b * T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = j + r * NS;
+                float2 y = v[b * R + brev(r, ilog2(R))];
+                if (centred) {
+                    const float2 c = tab[l];                      // exp(-j*pi*l/L)
+                    y = cmul(y, (l & 1) ? make_float2(-c.x, -c.y) : c);
+                }
+                tile[l * PL::TP + p] = y;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+
+// Range compression of pulses n0 .. n0+P-1 (those < n_az) into S[:, n0 .. n0+P), run by
+// blockDim.x == T*P threads with `smem` holding Tile<L, P>::SMEM_ELEMS elements.
+// build_tab = false reuses a twiddle table left in smem by a previous tile of the same L.
+template <int L, int P>
+__device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const float *__restrict__ win, int n_az,
+                                           bool centred, float2 *__restrict__ S, int n0, float2 *smem, bool build_tab,
+                                           bool vec_store) {
+    using PL = Tile<L, P>;
+    constexpr int RM = PL::RM, T = PL::T;
+    float2 *tab = smem;               // [2L] exp(-j*pi*q/L)
+    float2 *buf = smem + 2 * L;       // FFT buffer [P][LP], then transposed tile [L][TP]
+    const int t = threadIdx.x % T;
+    const int p = threadIdx.x / T;
+    const int n = n0 + p;
+
+    if (build_tab) {
+        for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
+            float s, c;
+            sincospif((float)q / (float)L, &s, &c);
+            tab[q] = make_float2(c, -s);
+        }
+    }
+
+    float2 v[RM];
+    {
+        const bool live = n < n_az;
+        const float2 *src = raw + (size_t)n * L;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int m = t + r * T;
+            const float2 x = live ? __ldg(src + m) : make_float2(0.f, 0.f);
+            const float wm = win ? __ldg(win + m) : 1.f;
+            v[r] = cscale(x, wm);
+        }
+    }
+    float2 *pb = buf + p * PL::LP;
+    constexpr int NF = PL::NF, RR = PL::RR;
+    if constexpr (L < 16) {
+        stockham_pass<L, P, L, 1, true, true>(v, t, p, pb, buf, tab, centred);
+    } else {
+        stockham_pass<L, P, 16, 1, true, (NF == 1 && RR == 1)>(v, t, p, pb, buf, tab, centred);
+        if constexpr (NF >= 2) stockham_pass<L, P, 16, 16, false, (NF == 2 && RR == 1)>(v, t, p, pb, buf, tab, centred);
+        if constexpr (NF >= 3) stockham_pass<L, P, 16, 256, false, (NF == 3 && RR == 1)>(v, t, p, pb, buf, tab, centred);
+        if constexpr (RR > 1) stockham_pass<L, P, RR, (L / RR), false, true>(v, t, p, pb, buf, tab, centred);
+    }
+
+    // coalesced store of the transposed tile: row l holds pulses n0..n0+P-1
+    const int np = min(P, n_az - n0);
+    if (vec_store && np == P) {
+        for (int idx = threadIdx.x; idx < L * (P / 2); idx += PL::THREADS) {
+            const int l = idx / (P / 2), q = idx % (P / 2);
+            const float4 val = *reinterpret_cast<const float4 *>(buf + l * PL::TP + 2 * q);
+            *reinterpret_cast<float4 *>(S + (size_t)l * n_az + n0 + 2 * q) = val;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < L * P; idx += PL::THREADS) {
+            const int l = idx / P, q = idx % P;
+            if (q < np) S[(size_t)l * n_az + n0 + q] = buf[l * PL::TP + q];
+        }
+    }
+}
+
+}  // namespace fft
+}  // namespace rosar

@@ -59,18 +59,33 @@ void synth_raw_cube(int n_az, int L, int n_sc,
             const double ph0 = frac_part(tau * (slope * t_start + fc));   /* cycles at m = 0 */
             const double dph = tau * slope * t_s;                          /* cycles per sample */
             const double are = a_re[t] * p, aim = a_im[t] * p;
-            const double rre = cos(TWO_PI * dph), rim = sin(TWO_PI * dph);
+            /* four interleaved chains z_{m+4} = z_m * rot^4 keep the recurrence off the critical path */
+            const double r1r = cos(TWO_PI * dph), r1i = sin(TWO_PI * dph);
+            const double r4r = cos(TWO_PI * 4.0 * dph), r4i = sin(TWO_PI * 4.0 * dph);
             for (int m0 = 0; m0 < L; m0 += 64) {
                 const double ph = TWO_PI * frac_part(ph0 + dph * (double)m0);
                 const double cr = cos(ph), ci = sin(ph);
-                double zr = are * cr - aim * ci, zi = are * ci + aim * cr;
+                double zr[4], zi[4];
+                zr[0] = are * cr - aim * ci;
+                zi[0] = are * ci + aim * cr;
+                for (int c = 1; c < 4; ++c) {
+                    zr[c] = zr[c - 1] * r1r - zi[c - 1] * r1i;
+                    zi[c] = zr[c - 1] * r1i + zi[c - 1] * r1r;
+                }
                 const int m1 = (m0 + 64 < L) ? m0 + 64 : L;
-                for (int m = m0; m < m1; ++m) {
-                    row[2 * m] += zr;
-                    row[2 * m + 1] += zi;
-                    const double nr = zr * rre - zi * rim;
-                    zi = zr * rim + zi * rre;
-                    zr = nr;
+                int m = m0;
+                for (; m + 4 <= m1; m += 4) {
+                    for (int c = 0; c < 4; ++c) {
+                        row[2 * (m + c)] += zr[c];
+                        row[2 * (m + c) + 1] += zi[c];
+                        const double nr = zr[c] * r4r - zi[c] * r4i;
+                        zi[c] = zr[c] * r4i + zi[c] * r4r;
+                        zr[c] = nr;
+                    }
+                }
+                for (int c = 0; m < m1; ++m, ++c) {
+                    row[2 * m] += zr[c];
+                    row[2 * m + 1] += zi[c];
                 }
             }
         }

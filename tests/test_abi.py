@@ -93,3 +93,26 @@ def test_binding_refuses_cpu_tensors():
     raw = torch.zeros((8, 64), dtype=torch.complex64)
     with pytest.raises(ValueError, match="CUDA"):
         rosar.range_compress(raw)
+
+
+def test_batch_create_rejects_bad_arguments(lib):
+    from paper_2309_08038_gb300 import _lib as L
+    ws = ctypes.c_void_p(0x40000000)
+    h = ctypes.c_void_p()
+    n = lib.rosar_batch_workspace_bytes(2)
+    assert n > 0 and lib.rosar_batch_workspace_bytes(0) == 0
+    scans = (L.ScanStruct * 2)()
+    for s in scans:
+        s.raw, s.w, s.o, s.S, s.out = 0x10000, 0x20000, 0x30000, 0x40000, 0x50000
+        s.n_az, s.L, s.K = 100, 64, 4
+    assert lib.rosar_batch_create(scans, 2, None, ws, n - 1, ctypes.byref(h)) == 1          # workspace too small
+    assert lib.rosar_batch_create(scans, 2, None, ctypes.c_void_p(0x40000010), n, ctypes.byref(h)) == 1  # alignment
+    scans[1].L = 4096
+    assert lib.rosar_batch_create(scans, 2, None, ws, n, ctypes.byref(h)) == 2              # L out of range
+    scans[1].L = 64
+    scans[0].o = None
+    assert lib.rosar_batch_create(scans, 2, None, ws, n, ctypes.byref(h)) == 1              # null offsets
+    scans[0].o = 0x30000
+    t = L.BatchTuningStruct(300, 0, 0, 0, -1)
+    assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1   # az_tile
+    assert h.value is None
