@@ -142,6 +142,41 @@ ROSAR_API rosar_status rosar_image(const rosar_c32 *raw, const float *win, const
                          rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Frequency-domain form of the sparse azimuth filter.  Eq. (43) with a fixed
+ * row is a circular convolution of S[r][.] with g_r, g_r[(-o_k) mod n_az] += w[r][k];
+ * it equals IFFT(H_r * FFT(S[r][.])) with H_r = FFT(g_r)/n_az.  H depends only on
+ * the weight design, so it is computed once (rosar_azimuth_plan) and reused for
+ * every scan.  Results equal rosar_sparse_azimuth up to float32 rounding
+ * (a different summation order); cost is O(log n_az) per pixel instead of O(K).
+ * ------------------------------------------------------------------------ */
+
+/* 1 if n_az = 2^a 3^b 5^c with 2 <= n_az <= 16384 (the sizes the FFT form handles), else 0. */
+ROSAR_API int rosar_azimuth_fft_supported(int n_az);
+
+/*
+ *   w, o, o_row_stride, n_rng, n_az, K: as rosar_sparse_azimuth                (in)
+ *   H    [n_rng][n_az] complex transfer functions FFT(g_r)/n_az, each row stored in
+ *        the library's internal (digit-reversed) frequency order: an opaque table
+ *        for rosar_sparse_azimuth_fft / rosar_image_fft.  H[r][0] is the DC term.  (out)
+ * ROSAR_ERR_UNSUPPORTED if rosar_azimuth_fft_supported(n_az) is 0.
+ */
+ROSAR_API rosar_status rosar_azimuth_plan(const rosar_c32 *w, const int32_t *o, int o_row_stride, int n_rng,
+                                          int n_az, int K, rosar_c32 *H, void *stream);
+
+/*
+ * out[r][.] = IFFT(H[r][.] * FFT(S[r][.])) for every row: rosar_sparse_azimuth with the
+ * weights and offsets that produced H.
+ *   S [n_rng][n_az] (in); H [n_rng][n_az] from rosar_azimuth_plan (in); out [n_rng][n_az] (out)
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth_fft(const rosar_c32 *S, const rosar_c32 *H, int n_rng, int n_az,
+                                                rosar_c32 *out, void *stream);
+
+/* rosar_image with the frequency-domain azimuth filter: range compression into
+ * `workspace`, then rosar_sparse_azimuth_fft over the L rows with H [L][n_az]. */
+ROSAR_API rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int n_az, int L,
+                                       rosar_c32 *workspace, rosar_c32 *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched form: many scans of uneven n_az, L and K imaged by ONE persistent
  * kernel launch, captured once in a CUDA graph.
  *

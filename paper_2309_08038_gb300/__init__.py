@@ -6,7 +6,8 @@ include/rosar.h); this package is its thin Python binding.  Build it with
 """
 
 from ._lib import LIB_PATH, RosarError, load  # noqa: F401
-from .ops import Radar, bpa, image, image_noalloc, range_compress, sparse_azimuth  # noqa: F401
+from .ops import (Radar, azimuth_fft_supported, azimuth_plan, bpa, image, image_fft, image_noalloc,  # noqa: F401
+                  range_compress, sparse_azimuth, sparse_azimuth_fft)
 from .batch import Batch, Tuning  # noqa: F401
 
 __version__ = "0.1.0"

@@ -140,7 +140,7 @@ KernelFn kernel_for(int J) {
     }
 }
 
-unsigned long long g_smem_done[4] = {0, 0, 0, 0};
+int g_smem_done[4][kMaxDevices] = {};
 
 int j_index(int J) { return J == 1 ? 0 : J == 2 ? 1 : J == 4 ? 2 : 3; }
 
@@ -289,7 +289,7 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
     if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "batch_create: descriptor copy: %s", cudaGetErrorString(e));
 
     KernelFn fn = kernel_for(J);
-    st = ensure_smem((const void *)fn, (size_t)smem, &g_smem_done[j_index(J)], "batch_create");
+    st = ensure_smem((const void *)fn, (size_t)smem, g_smem_done[j_index(J)], "batch_create");
     if (st != ROSAR_OK) return st;
     int dev = 0, n_sm = 0, occ = 0;
     e = cudaGetDevice(&dev);

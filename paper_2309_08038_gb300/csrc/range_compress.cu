@@ -38,8 +38,8 @@ rosar_status launch_L(const float2 *raw, const float *win, int n_az, int centred
     using PL = Plan<L>;
     static_assert(PL::SMEM <= 227 * 1024, "range-compress tile exceeds shared memory");
     if (PL::SMEM > 48 * 1024) {
-        static unsigned long long done = 0;
-        rosar_status st = ensure_smem((const void *)range_compress_kernel<L>, PL::SMEM, &done, "range_compress");
+        static int done[kMaxDevices] = {};
+        rosar_status st = ensure_smem((const void *)range_compress_kernel<L>, PL::SMEM, done, "range_compress");
         if (st != ROSAR_OK) return st;
     }
     const int grid = (n_az + PL::P - 1) / PL::P;

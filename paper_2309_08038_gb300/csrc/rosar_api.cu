@@ -27,16 +27,19 @@ rosar_status check_launch(const char *what) {
     return ROSAR_OK;
 }
 
-rosar_status ensure_smem(const void *func, size_t bytes, unsigned long long *done, const char *what) {
+rosar_status ensure_smem(const void *func, size_t bytes, int *limits, const char *what) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "%s: cudaGetDevice: %s", what, cudaGetErrorString(e));
-    const unsigned long long bit = 1ULL << (dev & 63);
-    if (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit) return ROSAR_OK;
+    if (dev < 0 || dev >= kMaxDevices) return set_error(ROSAR_ERR_UNSUPPORTED, "%s: device ordinal %d", what, dev);
+    if ((size_t)__atomic_load_n(limits + dev, __ATOMIC_ACQUIRE) >= bytes) return ROSAR_OK;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess)
         return set_error(ROSAR_ERR_CUDA, "%s: cudaFuncSetAttribute(%zu B): %s", what, bytes, cudaGetErrorString(e));
-    __atomic_fetch_or(done, bit, __ATOMIC_ACQ_REL);
+    int cur = __atomic_load_n(limits + dev, __ATOMIC_ACQUIRE);
+    while (cur < (int)bytes && !__atomic_compare_exchange_n(limits + dev, &cur, (int)bytes, false, __ATOMIC_ACQ_REL,
+                                                            __ATOMIC_ACQUIRE)) {
+    }
     return ROSAR_OK;
 }
 
@@ -170,6 +173,59 @@ rosar_status rosar_image(const rosar_c32 *raw, const float *win, const rosar_c32
     if (st != ROSAR_OK) return st;
     return launch_sparse_azimuth(reinterpret_cast<const float2 *>(workspace), reinterpret_cast<const float2 *>(w), o,
                                  o_row_stride, L, n_az, K, reinterpret_cast<float2 *>(out), s);
+}
+
+int rosar_azimuth_fft_supported(int n_az) { return azimuth_fft_supported(n_az); }
+
+rosar_status rosar_azimuth_plan(const rosar_c32 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
+                                rosar_c32 *H, void *stream) {
+    clear_error();
+    if (!w || !o || !H) return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan: null pointer argument");
+    if (n_rng < 1 || n_az < 1 || K < 1 || (o_row_stride != 0 && o_row_stride < K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan: n_rng=%d n_az=%d K=%d o_row_stride=%d", n_rng, n_az, K,
+                         o_row_stride);
+    if ((long long)n_rng * n_az > kMaxElems) return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_plan: H too large");
+    if (misaligned(w, 8) || misaligned(o, 4) || misaligned(H, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan: misaligned pointer");
+    const size_t hb = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    if (overlaps(H, hb, w, sizeof(rosar_c32) * (size_t)n_rng * K)) return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan: H overlaps w");
+    return launch_azimuth_plan(reinterpret_cast<const float2 *>(w), o, o_row_stride, n_rng, n_az, K,
+                               reinterpret_cast<float2 *>(H), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sparse_azimuth_fft(const rosar_c32 *S, const rosar_c32 *H, int n_rng, int n_az, rosar_c32 *out,
+                                      void *stream) {
+    clear_error();
+    if (!S || !H || !out) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft: null pointer argument");
+    if (n_rng < 1 || n_az < 1) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft: n_rng=%d n_az=%d", n_rng, n_az);
+    if ((long long)n_rng * n_az > kMaxElems) return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth_fft: too large");
+    if (misaligned(S, 8) || misaligned(H, 8) || misaligned(out, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft: misaligned pointer");
+    const size_t img = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    if (overlaps(out, img, S, img) || overlaps(out, img, H, img))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft: out overlaps an input");
+    return launch_azimuth_fft(reinterpret_cast<const float2 *>(S), reinterpret_cast<const float2 *>(H), n_rng, n_az,
+                              reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int n_az, int L,
+                             rosar_c32 *workspace, rosar_c32 *out, void *stream) {
+    clear_error();
+    rosar_status st = check_range_args(raw, win, n_az, L, workspace);
+    if (st != ROSAR_OK) return st;
+    if (!H || !out) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft: null H or out");
+    if (misaligned(H, 8) || misaligned(out, 8)) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft: misaligned pointer");
+    const size_t bytes = sizeof(rosar_c32) * (size_t)n_az * L;
+    if (overlaps(out, bytes, workspace, bytes) || overlaps(out, bytes, raw, bytes) || overlaps(out, bytes, H, bytes))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft: out overlaps an input");
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "image_fft: n_az=%d is not 2^a 3^b 5^c <= 16384", n_az);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = launch_range_compress(reinterpret_cast<const float2 *>(raw), win, n_az, L, 1,
+                               reinterpret_cast<float2 *>(workspace), s);
+    if (st != ROSAR_OK) return st;
+    return launch_azimuth_fft(reinterpret_cast<const float2 *>(workspace), reinterpret_cast<const float2 *>(H), L,
+                              n_az, reinterpret_cast<float2 *>(out), s);
 }
 
 }  // extern "C"

@@ -19,9 +19,10 @@ rosar_status check_launch(const char *what);
 
 static inline bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
-// Raises a kernel's dynamic shared-memory limit to `bytes` once per device.
-// `done` is a per-kernel bit mask of devices already configured.
-rosar_status ensure_smem(const void *func, size_t bytes, unsigned long long *done, const char *what);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// `limits` is a per-kernel array of kMaxDevices ints holding the limit set so far per device.
+constexpr int kMaxDevices = 64;
+rosar_status ensure_smem(const void *func, size_t bytes, int *limits, const char *what);
 
 // ------------------------------------------------------------ complex ops --
 
@@ -54,6 +55,12 @@ rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az
 
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
                                    int n_rng, int n_az, int K, float2 *out, cudaStream_t s);
+
+// Azimuth filter in the frequency domain (azimuth_fft.cu).
+int azimuth_fft_supported(int n_az);
+rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s);
+rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
+                                 float2 *H, cudaStream_t s);
 
 struct BpaParams {
     float inv_dR;        // 1/dR, bins per metre

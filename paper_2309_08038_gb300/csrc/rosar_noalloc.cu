@@ -26,7 +26,6 @@ namespace {
 
 static __device__ __align__(256) float2 g_noalloc_scratch[ROSAR_NOALLOC_MAX_ELEMS];
 
-constexpr int kMaxDevices = 64;
 float2 *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 

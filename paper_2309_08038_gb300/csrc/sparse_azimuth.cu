@@ -26,8 +26,8 @@ sparse_azimuth_kernel(const float2 *__restrict__ S, const float2 *__restrict__ w
 
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride, int n_rng,
                                    int n_az, int K, float2 *out, cudaStream_t s) {
-    static unsigned long long done = 0;
-    rosar_status st = ensure_smem((const void *)sparse_azimuth_kernel, SaGeo::SMEM_BYTES, &done, "sparse_azimuth");
+    static int done[kMaxDevices] = {};
+    rosar_status st = ensure_smem((const void *)sparse_azimuth_kernel, SaGeo::SMEM_BYTES, done, "sparse_azimuth");
     if (st != ROSAR_OK) return st;
     if (n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth: n_rng=%d exceeds 65535", n_rng);
     dim3 grid((n_az + SaGeo::TW - 1) / SaGeo::TW, n_rng);

@@ -137,3 +137,52 @@ def image_noalloc(raw, win, w, o, out=None, stream=None):
     check(lib.rosar_image_noalloc(ptr(raw), ptr(win), ptr(w), ptr(o), stride, n_az, L, K, ptr(out),
                                   stream_handle(stream)))
     return out
+
+
+def azimuth_fft_supported(n_az: int) -> bool:
+    """True if the frequency-domain azimuth filter handles n_az (2^a 3^b 5^c <= 16384)."""
+    return bool(_lib.load().rosar_azimuth_fft_supported(int(n_az)))
+
+
+def azimuth_plan(w, o, n_az, out=None, stream=None):
+    """rosar_azimuth_plan: H [n_rng, n_az] = FFT(g_r)/n_az for the weights w [n_rng, K] and offsets o."""
+    lib = _lib.load()
+    require(w, torch.complex64, "w", ndim=2)
+    n_rng, K = w.shape
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=w.device)
+    require(out, torch.complex64, "H", shape=(n_rng, n_az))
+    check(lib.rosar_azimuth_plan(ptr(w), ptr(o), stride, n_rng, n_az, K, ptr(out), stream_handle(stream)))
+    return out
+
+
+def sparse_azimuth_fft(S, H, out=None, stream=None):
+    """rosar_sparse_azimuth_fft: the sparse azimuth filter of S [n_rng, n_az] through its plan H."""
+    lib = _lib.load()
+    require(S, torch.complex64, "S", ndim=2)
+    n_rng, n_az = S.shape
+    require(H, torch.complex64, "H", shape=(n_rng, n_az))
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=S.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_fft(ptr(S), ptr(H), n_rng, n_az, ptr(out), stream_handle(stream)))
+    return out
+
+
+def image_fft(raw, win, H, workspace=None, out=None, stream=None):
+    """rosar_image_fft: range compression, then the frequency-domain azimuth filter with plan H [L, n_az]."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(H, torch.complex64, "H", shape=(L, n_az))
+    if workspace is None:
+        workspace = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    require(workspace, torch.complex64, "workspace", shape=(L, n_az))
+    require(out, torch.complex64, "out", shape=(L, n_az))
+    check(lib.rosar_image_fft(ptr(raw), ptr(win), ptr(H), n_az, L, ptr(workspace), ptr(out), stream_handle(stream)))
+    return out
