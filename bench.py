@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the BPA comparison lines")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-scan batched comparison")
     ap.add_argument("--gather", action="store_true", help="time the gather-MAC azimuth path instead of the FFT form")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-form comparison")
     return ap.parse_args()
 
 
@@ -191,6 +192,56 @@ def batched_inputs(torch, device):
                       "win": torch.from_numpy(synth.hann_window(c.L)).to(device)})
     del cubes
     return cfgs, scans
+
+
+def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_scans=16):
+    """Differentiable form: 16 indoor-geometry scans with per-pulse phase errors N(0, 0.3 rad) on the raw
+    cube; one step = images of the 16 scans, loss ||image - BPA image||^2 against the detached BPA image
+    of the error-free scans, and its gradient in the shared weights [256, 64] and the phase corrections
+    [16, 3600]."""
+    import numpy as np
+    rng = np.random.default_rng(200)
+    r = cfg.radar
+    radar = rosar.Radar(r.fc, r.slope, r.t_sample(cfg.L), r.t_start, r.r0, r.c)
+    raws, refs = [], []
+    S_stack = torch.empty((n_scans, cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
+    Bref = torch.empty_like(S_stack)
+    for s in range(n_scans):
+        clean = torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, 97 * s, axis=0))).to(device)
+        rosar.range_compress(clean, win, out=S_stack[s])
+        rosar.bpa(S_stack[s], radar, cfg.L, cfg.M_ap, out=Bref[s])
+        phi = torch.from_numpy(rng.standard_normal(cfg.n_az).astype(np.float32) * 0.3).to(device)
+        raws.append((clean * torch.exp(1j * phi)[:, None]).contiguous())
+    Bref /= torch.linalg.vector_norm(Bref) / torch.linalg.vector_norm(S_stack)     # comparable scale, detached
+    eps = torch.zeros((n_scans, cfg.n_az), dtype=torch.float32, device=device, requires_grad=True)
+    wp = w.clone().requires_grad_(True)
+
+    def forward():
+        for s in range(n_scans):
+            rosar.range_compress(raws[s], win, out=S_stack[s])
+        return rosar.autograd.sparse_azimuth_phase(S_stack, eps, wp, o)
+
+    def fwd_only(i):
+        with torch.no_grad():
+            forward()
+
+    def fwd_bwd(i):
+        wp.grad = None
+        eps.grad = None
+        out = forward()
+        loss = torch.sum(torch.abs(out - Bref) ** 2)
+        loss.backward()
+
+    n = 5
+    ms_f, _ = time_loop(torch, fwd_only, n, 2, stream, world, device)
+    ms_b, _ = time_loop(torch, fwd_bwd, n, 2, stream, world, device)
+    t_f, t_b = ms_f / n * 1e-3, ms_b / n * 1e-3
+    pix = n_scans * px
+    return {"scans": n_scans, "pixels": pix, "fwd_px_s": world * pix / t_f, "fwd_bwd_px_s": world * pix / t_b,
+            "ms_fwd": t_f * 1e3, "ms_fwd_bwd": t_b * 1e3, "bwd_over_fwd": (t_b - t_f) / t_f,
+            "grad_finite": bool(torch.isfinite(wp.grad).all().item() and torch.isfinite(eps.grad).all().item()),
+            "note": "step = 16 range compressions + phase-corrected gather filter (forward), torch loss, "
+                    "adjoint gather + weight-gradient + phase-gradient kernels (backward)"}
 
 
 def time_loop(torch, fn, steps, warmup, stream, world, device):
@@ -458,6 +509,10 @@ def run_ours(args):
         b.close()
         del bscans, sc_ws
 
+    diff = {}
+    if not args.no_diff:
+        diff = diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_subprocess()
@@ -484,6 +539,7 @@ def run_ours(args):
             "e2e": e2e,
             "compare": compare,
             "batched": batched,
+            "diff": diff,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
         }

@@ -177,6 +177,56 @@ ROSAR_API rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, c
                                        rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Differentiable form: a stack of n_scans scans [n_scans][n_rng][n_az] that share
+ * one weight set, a per-pulse phase correction eps [n_scans][n_az] applied to the
+ * range-compressed data, and the adjoints that give the gradient of a real image
+ * loss with respect to the weights, the phase corrections, S and the raw cube.
+ *   forward:  S_t = S * exp(j*eps[n])  (rosar_phase_apply), then
+ *             out[s][r][t] = sum_k w[r][k] * S_t[s][r][(t + o_k) mod n_az]  (rosar_sparse_azimuth_scans)
+ * Gradients follow the conjugate-Wirtinger convention of torch: for a real loss and a
+ * holomorphic linear map y = A x, grad_x = A^H grad_y; for the real eps, the ordinary
+ * derivative.  Every reduction runs in a fixed order (bit-reproducible).
+ * ------------------------------------------------------------------------ */
+
+/* S_t[s][r][n] = S[s][r][n] * exp(j*eps[s][n]); S_t may equal S (in place). */
+ROSAR_API rosar_status rosar_phase_apply(const rosar_c32 *S, const float *eps, int n_scans, int n_rng, int n_az,
+                                         rosar_c32 *S_t, void *stream);
+
+/* rosar_sparse_azimuth over each scan of the stack with the shared w [n_rng][K] and o. */
+ROSAR_API rosar_status rosar_sparse_azimuth_scans(const rosar_c32 *S, const rosar_c32 *w, const int32_t *o,
+                                                  int o_row_stride, int n_scans, int n_rng, int n_az, int K,
+                                                  rosar_c32 *out, void *stream);
+
+/*
+ * Adjoint of Eq. (43) for the gradient g = d loss / d conj(out) [n_scans][n_rng][n_az]:
+ *   grad_S_t[s][r][n] = sum_k conj(w[r][k]) * g[s][r][(n - o_k) mod n_az]        (NULL to skip)
+ *   grad_w[r][k]      = sum_s sum_t g[s][r][t] * conj(S_t[s][r][(t + o_k) mod n_az])  (NULL to skip;
+ *                       needs S_t, the forward's phase-corrected input)
+ * grad_S_t is the transposed gather (conjugated weights, negated offsets); grad_w is a
+ * per-(row, tap) reduction over scans and azimuth.
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth_adjoint(const rosar_c32 *g, const rosar_c32 *S_t, const rosar_c32 *w,
+                                                    const int32_t *o, int o_row_stride, int n_scans, int n_rng,
+                                                    int n_az, int K, rosar_c32 *grad_S_t, rosar_c32 *grad_w,
+                                                    void *stream);
+
+/*
+ * grad_eps[s][n] = sum_r Im(conj(S_t[s][r][n]) * grad_S_t[s][r][n])   (NULL to skip)
+ * grad_S[s][r][n] = grad_S_t[s][r][n] * exp(-j*eps[s][n])             (NULL to skip; needs eps)
+ */
+ROSAR_API rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *grad_S_t, const float *eps,
+                                        int n_scans, int n_rng, int n_az, float *grad_eps, rosar_c32 *grad_S,
+                                        void *stream);
+
+/*
+ * Adjoint of rosar_range_compress (Eq. (38) transposed):
+ *   grad_raw[n][m] = win[m] * sum_l conj(c_l) * exp(+j*2*pi*l*m/L) * g[l][n]
+ *   g [L][n_az] range-major (in); grad_raw [n_az][L] pulse-major (out).
+ */
+ROSAR_API rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, int n_az, int L,
+                                                    int centred, rosar_c32 *grad_raw, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched form: many scans of uneven n_az, L and K imaged by ONE persistent
  * kernel launch, captured once in a CUDA graph.
  *

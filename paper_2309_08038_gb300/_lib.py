@@ -56,6 +56,11 @@ _PROTOS = {
     "rosar_azimuth_plan": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_fft": (_I, [_P, _P, _I, _I, _P, _P]),
     "rosar_image_fft": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "rosar_phase_apply": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "rosar_sparse_azimuth_scans": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "rosar_sparse_azimuth_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_phase_grad": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "rosar_range_compress_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "rosar_batch_workspace_bytes": (ctypes.c_size_t, [_I]),
     "rosar_batch_create": (_I, [ctypes.POINTER(ScanStruct), _I, ctypes.POINTER(BatchTuningStruct), _P,
                                 ctypes.c_size_t, ctypes.POINTER(_P)]),

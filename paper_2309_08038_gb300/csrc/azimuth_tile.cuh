@@ -36,6 +36,15 @@ __device__ __forceinline__ int canon_offset(int o, int n) {
     return (c > n / 2) ? c - n : c;
 }
 
+// Offset of tap k as the tile uses it: o_k, or -o_k for the adjoint (transposed gather).
+template <bool ADJ>
+__device__ __forceinline__ int tap_offset(const int32_t *o, int n) {
+    const int v = __ldg(o);
+    if (!ADJ) return canon_offset(v, n);
+    const long long m = (-(long long)v) % n;      // -INT_MIN does not fit an int
+    return canon_offset((int)m, n);
+}
+
 // COHERENT: S was written earlier in the same kernel (read through L2, not the non-coherent path).
 template <bool COHERENT>
 __device__ __forceinline__ float2 load_s(const float2 *p) {
@@ -44,7 +53,9 @@ __device__ __forceinline__ float2 load_s(const float2 *p) {
 }
 
 // `smem` holds Geo<J>::SMEM_BYTES bytes; `red` 2*THREADS/32 ints.  Called by all 256 threads.
-template <int J, bool COHERENT>
+// ADJ: the adjoint in S, out[r][n] = sum_k conj(w[r][k]) * S[r][(n - o_k) mod n_az] (conjugated weights,
+// negated offsets), which is the scatter-add of the forward filter written as a gather.
+template <int J, bool COHERENT, bool ADJ = false>
 __device__ __forceinline__ void azimuth_tile(const float2 *__restrict__ S, const float2 *__restrict__ w,
                                              const int32_t *__restrict__ o, int o_row_stride, int n_az, int K,
                                              float2 *__restrict__ out, int r, int th0, char *smem, int *red) {
@@ -62,7 +73,7 @@ __device__ __forceinline__ void azimuth_tile(const float2 *__restrict__ S, const
     // span of the canonical offsets
     int lo = INT_MAX, hi = INT_MIN;
     for (int k = tid; k < K; k += THREADS) {
-        const int c = canon_offset(__ldg(orow + k), n_az);
+        const int c = tap_offset<ADJ>(orow + k, n_az);
         lo = min(lo, c);
         hi = max(hi, c);
     }
@@ -105,8 +116,9 @@ __device__ __forceinline__ void azimuth_tile(const float2 *__restrict__ S, const
         const int kc = min(KC, K - k0);
         __syncthreads();   // window staged / previous chunk consumed
         for (int i = tid; i < kc; i += THREADS) {
-            wk[i] = __ldg(wrow + k0 + i);
-            const int c = canon_offset(__ldg(orow + k0 + i), n_az);
+            const float2 wv = __ldg(wrow + k0 + i);
+            wk[i] = ADJ ? cconj(wv) : wv;
+            const int c = tap_offset<ADJ>(orow + k0 + i, n_az);
             rel[i] = staged ? c - lo : c;
         }
         __syncthreads();

@@ -1,0 +1,189 @@
+// Differentiable form: per-pulse phase correction and the adjoints of the sparse azimuth
+// filter (arXiv 2309.08038, Sec. III-D, Eq. (43)), for a stack of scans sharing one weight set.
+//
+// Forward (with the gather kernel in between):
+//   S_t[s][r][n]   = S[s][r][n] * exp(j * eps[s][n])                          (phase_apply)
+//   out[s][r][t]   = sum_k w[r][k] * S_t[s][r][(t + o_k) mod N]
+// Backward, conjugate-Wirtinger convention (grad of a real loss; grad_x = A^H grad_y):
+//   grad_S_t       = sum_k conj(w[r][k]) * g[s][r][(n - o_k) mod N]           (gather kernel, adjoint mode)
+//   grad_w[r][k]   = sum_s sum_t g[s][r][t] * conj(S_t[s][r][(t + o_k) mod N]) (weight_grad)
+//   grad_eps[s][n] = sum_r Im(conj(S_t[s][r][n]) * grad_S_t[s][r][n])          (phase_grad)
+//   grad_S         = grad_S_t * exp(-j * eps[s][n])                            (phase_grad, optional)
+// Every reduction runs in a fixed order (no atomics), so gradients are bit-reproducible.
+
+#include <limits.h>
+
+#include "rosar_internal.cuh"
+
+namespace rosar {
+namespace {
+
+constexpr int DG_THREADS = 256;
+
+// One thread per (scan, pulse): the phase factor is computed once and applied down the column.
+__global__ void __launch_bounds__(DG_THREADS)
+phase_apply_kernel(const float2 *__restrict__ S, const float *__restrict__ eps, int n_rng, int n_az,
+                   float2 *__restrict__ S_t) {
+    const int n = blockIdx.x * DG_THREADS + threadIdx.x;
+    const int s = blockIdx.y;
+    if (n >= n_az) return;
+    float sn, cs;
+    sincosf(__ldg(eps + (size_t)s * n_az + n), &sn, &cs);
+    const float2 e = make_float2(cs, sn);
+    const size_t base = (size_t)s * n_rng * n_az + n;
+#pragma unroll 4
+    for (int r = 0; r < n_rng; ++r) S_t[base + (size_t)r * n_az] = cmul(__ldg(S + base + (size_t)r * n_az), e);
+}
+
+__global__ void __launch_bounds__(DG_THREADS)
+phase_grad_kernel(const float2 *__restrict__ S_t, const float2 *__restrict__ G, const float *__restrict__ eps,
+                  int n_rng, int n_az, float *__restrict__ grad_eps, float2 *__restrict__ grad_S) {
+    const int n = blockIdx.x * DG_THREADS + threadIdx.x;
+    const int s = blockIdx.y;
+    if (n >= n_az) return;
+    const size_t base = (size_t)s * n_rng * n_az + n;
+    float2 e = make_float2(1.f, 0.f);
+    if (grad_S) {
+        float sn, cs;
+        sincosf(__ldg(eps + (size_t)s * n_az + n), &sn, &cs);
+        e = make_float2(cs, -sn);
+    }
+    float acc = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < n_rng; ++r) {
+        const float2 a = __ldg(S_t + base + (size_t)r * n_az);
+        const float2 b = __ldg(G + base + (size_t)r * n_az);
+        acc = fmaf(a.x, b.y, acc);          // Im(conj(a) * b) = a.x*b.y - a.y*b.x
+        acc = fmaf(-a.y, b.x, acc);
+        if (grad_S) grad_S[base + (size_t)r * n_az] = cmul(b, e);
+    }
+    if (grad_eps) grad_eps[(size_t)s * n_az + n] = acc;
+}
+
+// grad_w: one CTA per range row; warp q owns taps q, q+8, q+16, ... (up to WT per pass over the data).
+// Azimuth is processed in chunks of DG_CHUNK outputs: the gradient chunk and the circular window of
+// S_t it meets are staged in shared memory; each lane accumulates its strided share of theta for
+// every tap it owns, then the warp reduces in a fixed shuffle order.
+constexpr int DG_WARPS = DG_THREADS / 32;
+constexpr int DG_WT = 16;                       // taps per warp per sweep
+constexpr int DG_CHUNK = 1024;
+constexpr int DG_SPAN_CAP = 2560;
+
+__device__ __forceinline__ int canon(int o, int n) {
+    int c = pmod(o, n);
+    return (c > n / 2) ? c - n : c;
+}
+
+__global__ void __launch_bounds__(DG_THREADS)
+weight_grad_kernel(const float2 *__restrict__ g, const float2 *__restrict__ S_t, const int32_t *__restrict__ o,
+                   int o_row_stride, int n_scans, int n_rng, int n_az, int K, float2 *__restrict__ grad_w) {
+    __shared__ float2 gs[DG_CHUNK];
+    __shared__ float2 ws[DG_CHUNK + DG_SPAN_CAP];
+    __shared__ int red_lo[DG_WARPS], red_hi[DG_WARPS];
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t *orow = o + (size_t)r * o_row_stride;
+
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int k = threadIdx.x; k < K; k += DG_THREADS) {
+        const int c = canon(__ldg(orow + k), n_az);
+        lo = min(lo, c);
+        hi = max(hi, c);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, s));
+    }
+    if (lane == 0) {
+        red_lo[warp] = lo;
+        red_hi[warp] = hi;
+    }
+    __syncthreads();
+    lo = red_lo[0];
+    hi = red_hi[0];
+#pragma unroll
+    for (int i = 1; i < DG_WARPS; ++i) {
+        lo = min(lo, red_lo[i]);
+        hi = max(hi, red_hi[i]);
+    }
+    const bool staged = hi - lo <= DG_SPAN_CAP;
+
+    for (int k0 = 0; k0 < K; k0 += DG_WARPS * DG_WT) {
+        int rel[DG_WT];
+        float2 acc[DG_WT];
+#pragma unroll
+        for (int t = 0; t < DG_WT; ++t) {
+            const int k = k0 + warp + t * DG_WARPS;
+            const int c = k < K ? canon(__ldg(orow + k), n_az) : lo;
+            rel[t] = staged ? c - lo : c;
+            acc[t] = make_float2(0.f, 0.f);
+        }
+        for (int s = 0; s < n_scans; ++s) {
+            const size_t rowoff = ((size_t)s * n_rng + r) * n_az;
+            const float2 *grow = g + rowoff;
+            const float2 *srow = S_t + rowoff;
+            for (int t0 = 0; t0 < n_az; t0 += DG_CHUNK) {
+                const int cw = min(DG_CHUNK, n_az - t0);
+                __syncthreads();
+                for (int i = threadIdx.x; i < cw; i += DG_THREADS) gs[i] = __ldg(grow + t0 + i);
+                if (staged) {
+                    const int start = pmod(t0 + lo, n_az);
+                    for (int i = threadIdx.x; i < cw + hi - lo; i += DG_THREADS) {
+                        int idx = start + i;
+                        if (idx >= n_az) idx %= n_az;
+                        ws[i] = __ldg(srow + idx);
+                    }
+                }
+                __syncthreads();
+                for (int i = lane; i < cw; i += 32) {
+                    const float2 gv = gs[i];
+#pragma unroll
+                    for (int t = 0; t < DG_WT; ++t) {
+                        const float2 sv = staged ? ws[i + rel[t]] : __ldg(srow + pmod(t0 + i + rel[t], n_az));
+                        acc[t].x = fmaf(gv.x, sv.x, acc[t].x);       // g * conj(s)
+                        acc[t].x = fmaf(gv.y, sv.y, acc[t].x);
+                        acc[t].y = fmaf(gv.y, sv.x, acc[t].y);
+                        acc[t].y = fmaf(-gv.x, sv.y, acc[t].y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < DG_WT; ++t) {
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) {
+                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, sft);
+                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, sft);
+            }
+            const int k = k0 + warp + t * DG_WARPS;
+            if (lane == 0 && k < K) grad_w[(size_t)r * K + k] = acc[t];
+        }
+    }
+}
+
+}  // namespace
+
+rosar_status launch_phase_apply(const float2 *S, const float *eps, int n_scans, int n_rng, int n_az, float2 *S_t,
+                                cudaStream_t s) {
+    if (n_scans > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "phase_apply: n_scans=%d exceeds 65535", n_scans);
+    dim3 grid((n_az + DG_THREADS - 1) / DG_THREADS, n_scans);
+    phase_apply_kernel<<<grid, DG_THREADS, 0, s>>>(S, eps, n_rng, n_az, S_t);
+    return check_launch("phase_apply");
+}
+
+rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *eps, int n_scans, int n_rng, int n_az,
+                               float *grad_eps, float2 *grad_S, cudaStream_t s) {
+    if (n_scans > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "phase_grad: n_scans=%d exceeds 65535", n_scans);
+    dim3 grid((n_az + DG_THREADS - 1) / DG_THREADS, n_scans);
+    phase_grad_kernel<<<grid, DG_THREADS, 0, s>>>(S_t, G, eps, n_rng, n_az, grad_eps, grad_S);
+    return check_launch("phase_grad");
+}
+
+rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
+                                        int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s) {
+    weight_grad_kernel<<<n_rng, DG_THREADS, 0, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, n_az, K, grad_w);
+    return check_launch("azimuth_weight_grad");
+}
+
+}  // namespace rosar

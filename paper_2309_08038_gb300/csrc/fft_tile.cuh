@@ -206,5 +206,58 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
     }
 }
 
+// Adjoint of range_tile for pulses n0 .. n0+P-1 (Eq. (38) transposed, conjugate-Wirtinger convention):
+//   grad_raw[n][m] = win[m] * sum_l conj(c_l) * exp(+j*2*pi*l*m/L) * g[l][n]
+//                  = win[m] * conj( DFT_l{ c_l * conj(g[l][n]) }[m] ).
+// Reads the range-major gradient g [L][n_az] with loads coalesced along azimuth, runs the same
+// Stockham passes with every result kept in the per-pulse buffer (natural order), and writes
+// grad_raw [n_az][L] pulse-major.  blockDim.x == T*P; `smem` holds Tile<L, P>::SMEM_ELEMS elements.
+template <int L, int P>
+__device__ __forceinline__ void range_adjoint_tile(const float2 *__restrict__ g, const float *__restrict__ win,
+                                                   int n_az, bool centred, float2 *__restrict__ grad_raw, int n0,
+                                                   float2 *smem) {
+    using PL = Tile<L, P>;
+    constexpr int RM = PL::RM, T = PL::T;
+    float2 *tab = smem;
+    float2 *buf = smem + 2 * L;
+    const int t = threadIdx.x % T;
+    const int p = threadIdx.x / T;
+    const int np = min(P, n_az - n0);
+    for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
+        float s, c;
+        sincospif((float)q / (float)L, &s, &c);
+        tab[q] = make_float2(c, -s);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < L * P; idx += PL::THREADS) {
+        const int l = idx / P, q = idx % P;
+        float2 x = q < np ? cconj(__ldg(g + (size_t)l * n_az + n0 + q)) : make_float2(0.f, 0.f);
+        if (centred) {
+            const float2 c = tab[l];
+            x = cmul(x, (l & 1) ? make_float2(-c.x, -c.y) : c);
+        }
+        buf[q * PL::LP + pad16(l)] = x;
+    }
+    __syncthreads();
+    float2 v[RM];
+    float2 *pb = buf + p * PL::LP;
+    constexpr int NF = PL::NF, RR = PL::RR;
+    if constexpr (L < 16) {
+        stockham_pass<L, P, L, 1, false, false>(v, t, p, pb, buf, tab, false);
+    } else {
+        stockham_pass<L, P, 16, 1, false, false>(v, t, p, pb, buf, tab, false);
+        if constexpr (NF >= 2) stockham_pass<L, P, 16, 16, false, false>(v, t, p, pb, buf, tab, false);
+        if constexpr (NF >= 3) stockham_pass<L, P, 16, 256, false, false>(v, t, p, pb, buf, tab, false);
+        if constexpr (RR > 1) stockham_pass<L, P, RR, (L / RR), false, false>(v, t, p, pb, buf, tab, false);
+    }
+    for (int idx = threadIdx.x; idx < P * L; idx += PL::THREADS) {
+        const int q = idx / L, m = idx % L;
+        if (q < np) {
+            const float wm = win ? __ldg(win + m) : 1.f;
+            grad_raw[(size_t)(n0 + q) * L + m] = cscale(cconj(buf[q * PL::LP + pad16(m)]), wm);
+        }
+    }
+}
+
 }  // namespace fft
 }  // namespace rosar

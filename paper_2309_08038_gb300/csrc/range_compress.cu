@@ -34,6 +34,28 @@ range_compress_kernel(const float2 *__restrict__ raw, const float *__restrict__ 
 }
 
 template <int L>
+__global__ void __launch_bounds__(Plan<L>::THREADS)
+range_adjoint_kernel(const float2 *__restrict__ g, const float *__restrict__ win, int n_az, int centred,
+                     float2 *__restrict__ grad_raw) {
+    extern __shared__ float2 smem[];
+    fft::range_adjoint_tile<L, Plan<L>::P>(g, win, n_az, centred != 0, grad_raw, blockIdx.x * Plan<L>::P, smem);
+}
+
+template <int L>
+rosar_status launch_adjoint_L(const float2 *g, const float *win, int n_az, int centred, float2 *grad_raw,
+                              cudaStream_t s) {
+    using PL = Plan<L>;
+    if (PL::SMEM > 48 * 1024) {
+        static int done[kMaxDevices] = {};
+        rosar_status st = ensure_smem((const void *)range_adjoint_kernel<L>, PL::SMEM, done, "range_compress_adjoint");
+        if (st != ROSAR_OK) return st;
+    }
+    const int grid = (n_az + PL::P - 1) / PL::P;
+    range_adjoint_kernel<L><<<grid, PL::THREADS, PL::SMEM, s>>>(g, win, n_az, centred, grad_raw);
+    return check_launch("range_compress_adjoint");
+}
+
+template <int L>
 rosar_status launch_L(const float2 *raw, const float *win, int n_az, int centred, float2 *S, cudaStream_t s) {
     using PL = Plan<L>;
     static_assert(PL::SMEM <= 227 * 1024, "range-compress tile exceeds shared memory");
@@ -64,6 +86,24 @@ rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az
         case 2048: return launch_L<2048>(raw, win, n_az, centred, S, s);
         case 4096: return launch_L<4096>(raw, win, n_az, centred, S, s);
         default: return set_error(ROSAR_ERR_UNSUPPORTED, "range_compress: L=%d is not a power of two in [8, 4096]", L);
+    }
+}
+
+rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, int n_az, int L, int centred,
+                                           float2 *grad_raw, cudaStream_t s) {
+    switch (L) {
+        case 8: return launch_adjoint_L<8>(g, win, n_az, centred, grad_raw, s);
+        case 16: return launch_adjoint_L<16>(g, win, n_az, centred, grad_raw, s);
+        case 32: return launch_adjoint_L<32>(g, win, n_az, centred, grad_raw, s);
+        case 64: return launch_adjoint_L<64>(g, win, n_az, centred, grad_raw, s);
+        case 128: return launch_adjoint_L<128>(g, win, n_az, centred, grad_raw, s);
+        case 256: return launch_adjoint_L<256>(g, win, n_az, centred, grad_raw, s);
+        case 512: return launch_adjoint_L<512>(g, win, n_az, centred, grad_raw, s);
+        case 1024: return launch_adjoint_L<1024>(g, win, n_az, centred, grad_raw, s);
+        case 2048: return launch_adjoint_L<2048>(g, win, n_az, centred, grad_raw, s);
+        case 4096: return launch_adjoint_L<4096>(g, win, n_az, centred, grad_raw, s);
+        default:
+            return set_error(ROSAR_ERR_UNSUPPORTED, "range_compress_adjoint: L=%d is not a power of two in [8, 4096]", L);
     }
 }
 

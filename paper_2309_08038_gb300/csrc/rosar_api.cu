@@ -228,4 +228,99 @@ rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar
                               n_az, reinterpret_cast<float2 *>(out), s);
 }
 
+// ------------------------------------------------------------ differentiable form --
+
+namespace {
+
+rosar_status check_stack(const char *what, int n_scans, int n_rng, int n_az) {
+    if (n_scans < 1 || n_rng < 1 || n_az < 1)
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: n_scans=%d n_rng=%d n_az=%d must be >= 1", what, n_scans, n_rng,
+                         n_az);
+    if ((long long)n_scans * n_rng * n_az > kMaxElems) return set_error(ROSAR_ERR_UNSUPPORTED, "%s: stack too large", what);
+    return ROSAR_OK;
+}
+
+}  // namespace
+
+rosar_status rosar_phase_apply(const rosar_c32 *S, const float *eps, int n_scans, int n_rng, int n_az, rosar_c32 *S_t,
+                               void *stream) {
+    clear_error();
+    if (!S || !eps || !S_t) return set_error(ROSAR_ERR_INVALID_ARG, "phase_apply: null pointer argument");
+    rosar_status st = check_stack("phase_apply", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (misaligned(S, 8) || misaligned(S_t, 8) || misaligned(eps, 4))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phase_apply: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az;
+    if (S != S_t && overlaps(S, b, S_t, b)) return set_error(ROSAR_ERR_INVALID_ARG, "phase_apply: S and S_t partly overlap");
+    return launch_phase_apply(reinterpret_cast<const float2 *>(S), eps, n_scans, n_rng, n_az,
+                              reinterpret_cast<float2 *>(S_t), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sparse_azimuth_scans(const rosar_c32 *S, const rosar_c32 *w, const int32_t *o, int o_row_stride,
+                                        int n_scans, int n_rng, int n_az, int K, rosar_c32 *out, void *stream) {
+    clear_error();
+    rosar_status st = check_stack("sparse_azimuth_scans", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    st = check_azimuth_args(S, w, o, o_row_stride, n_rng, n_az, K, out);
+    if (st != ROSAR_OK) return st;
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az;
+    if (overlaps(out, b, S, b)) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_scans: out overlaps S");
+    return launch_sparse_azimuth_scans(reinterpret_cast<const float2 *>(S), reinterpret_cast<const float2 *>(w), o,
+                                       o_row_stride, n_scans, n_rng, n_az, K, false, reinterpret_cast<float2 *>(out),
+                                       static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sparse_azimuth_adjoint(const rosar_c32 *g, const rosar_c32 *S_t, const rosar_c32 *w,
+                                          const int32_t *o, int o_row_stride, int n_scans, int n_rng, int n_az, int K,
+                                          rosar_c32 *grad_S_t, rosar_c32 *grad_w, void *stream) {
+    clear_error();
+    rosar_status st = check_stack("sparse_azimuth_adjoint", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!g || !w || !o || (!grad_S_t && !grad_w) || (grad_w && !S_t))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_adjoint: null pointer argument");
+    if (K < 1 || (o_row_stride != 0 && o_row_stride < K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_adjoint: K=%d o_row_stride=%d", K, o_row_stride);
+    if (misaligned(g, 8) || misaligned(w, 8) || misaligned(o, 4) || (S_t && misaligned(S_t, 8)) ||
+        (grad_S_t && misaligned(grad_S_t, 8)) || (grad_w && misaligned(grad_w, 8)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_adjoint: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az;
+    if (grad_S_t && (overlaps(grad_S_t, b, g, b) || (S_t && overlaps(grad_S_t, b, S_t, b))))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_adjoint: grad_S_t overlaps an input");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grad_S_t) {
+        st = launch_sparse_azimuth_scans(reinterpret_cast<const float2 *>(g), reinterpret_cast<const float2 *>(w), o,
+                                         o_row_stride, n_scans, n_rng, n_az, K, true,
+                                         reinterpret_cast<float2 *>(grad_S_t), s);
+        if (st != ROSAR_OK) return st;
+    }
+    if (grad_w)
+        st = launch_azimuth_weight_grad(reinterpret_cast<const float2 *>(g), reinterpret_cast<const float2 *>(S_t), o,
+                                        o_row_stride, n_scans, n_rng, n_az, K, reinterpret_cast<float2 *>(grad_w), s);
+    return st;
+}
+
+rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *grad_S_t, const float *eps, int n_scans,
+                              int n_rng, int n_az, float *grad_eps, rosar_c32 *grad_S, void *stream) {
+    clear_error();
+    if (!S_t || !grad_S_t || (!grad_eps && !grad_S) || (grad_S && !eps))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phase_grad: null pointer argument");
+    rosar_status st = check_stack("phase_grad", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (misaligned(S_t, 8) || misaligned(grad_S_t, 8) || (eps && misaligned(eps, 4)) ||
+        (grad_eps && misaligned(grad_eps, 4)) || (grad_S && misaligned(grad_S, 8)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phase_grad: misaligned pointer");
+    return launch_phase_grad(reinterpret_cast<const float2 *>(S_t), reinterpret_cast<const float2 *>(grad_S_t), eps,
+                             n_scans, n_rng, n_az, grad_eps, reinterpret_cast<float2 *>(grad_S),
+                             static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, int n_az, int L, int centred,
+                                          rosar_c32 *grad_raw, void *stream) {
+    clear_error();
+    rosar_status st = check_range_args(g, win, n_az, L, grad_raw);
+    if (st != ROSAR_OK) return st;
+    return launch_range_compress_adjoint(reinterpret_cast<const float2 *>(g), win, n_az, L, centred,
+                                         reinterpret_cast<float2 *>(grad_raw), static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

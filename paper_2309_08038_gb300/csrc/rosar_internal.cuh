@@ -56,6 +56,21 @@ rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
                                    int n_rng, int n_az, int K, float2 *out, cudaStream_t s);
 
+// Stacked scans [n_scans][n_rng][n_az] sharing w and o; adjoint = conjugated weights, negated offsets.
+rosar_status launch_sparse_azimuth_scans(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
+                                         int n_scans, int n_rng, int n_az, int K, bool adjoint, float2 *out,
+                                         cudaStream_t s);
+
+// Differentiable form (diff.cu, range_compress.cu).
+rosar_status launch_phase_apply(const float2 *S, const float *eps, int n_scans, int n_rng, int n_az, float2 *S_t,
+                                cudaStream_t s);
+rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
+                                        int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s);
+rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *eps, int n_scans, int n_rng, int n_az,
+                               float *grad_eps, float2 *grad_S, cudaStream_t s);
+rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, int n_az, int L, int centred,
+                                           float2 *grad_raw, cudaStream_t s);
+
 // Azimuth filter in the frequency domain (azimuth_fft.cu).
 int azimuth_fft_supported(int n_az);
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s);

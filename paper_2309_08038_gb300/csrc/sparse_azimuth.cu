@@ -2,9 +2,10 @@
 //
 //   out[r][theta] = sum_{k<K} w[r][k] * S[r][(theta + o_k) mod n_az]
 //
-// Grid: (azimuth tiles of TW = 1024 outputs, range rows); each CTA runs one
+// Grid: (azimuth tiles of TW = 1024 outputs, range rows, scans); each CTA runs one
 // gather-MAC tile (azimuth_tile.cuh): the row's circular window staged in shared
-// memory, 4 outputs per thread, taps broadcast from shared memory.
+// memory, 4 outputs per thread, taps broadcast from shared memory.  The same
+// kernel with conjugated weights and negated offsets is the adjoint in S.
 
 #include "azimuth_tile.cuh"
 
@@ -14,25 +15,43 @@ namespace {
 constexpr int SA_J = 4;
 using SaGeo = az::Geo<SA_J>;
 
+// blockIdx = (azimuth tile, range row, scan); scans are stacked [n_scans][n_rng][n_az] and share w, o.
+template <bool ADJ>
 __global__ void __launch_bounds__(az::THREADS)
 sparse_azimuth_kernel(const float2 *__restrict__ S, const float2 *__restrict__ w, const int32_t *__restrict__ o,
-                      int o_row_stride, int n_az, int K, float2 *__restrict__ out) {
+                      int o_row_stride, int n_rng, int n_az, int K, float2 *__restrict__ out) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int red[2 * az::THREADS / 32];
-    az::azimuth_tile<SA_J, false>(S, w, o, o_row_stride, n_az, K, out, blockIdx.y, blockIdx.x * SaGeo::TW, sm, red);
+    const size_t scan = (size_t)blockIdx.z * n_rng * n_az;
+    az::azimuth_tile<SA_J, false, ADJ>(S + scan, w, o, o_row_stride, n_az, K, out + scan, blockIdx.y,
+                                       blockIdx.x * SaGeo::TW, sm, red);
+}
+
+template <bool ADJ>
+rosar_status launch_gather(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride, int n_scans,
+                           int n_rng, int n_az, int K, float2 *out, cudaStream_t s) {
+    static int done[kMaxDevices] = {};
+    rosar_status st = ensure_smem((const void *)sparse_azimuth_kernel<ADJ>, SaGeo::SMEM_BYTES, done, "sparse_azimuth");
+    if (st != ROSAR_OK) return st;
+    if (n_rng > 65535 || n_scans > 65535)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth: n_rng=%d or n_scans=%d exceeds 65535", n_rng, n_scans);
+    dim3 grid((n_az + SaGeo::TW - 1) / SaGeo::TW, n_rng, n_scans);
+    sparse_azimuth_kernel<ADJ><<<grid, az::THREADS, SaGeo::SMEM_BYTES, s>>>(S, w, o, o_row_stride, n_rng, n_az, K, out);
+    return check_launch(ADJ ? "sparse_azimuth_adjoint" : "sparse_azimuth");
 }
 
 }  // namespace
 
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride, int n_rng,
                                    int n_az, int K, float2 *out, cudaStream_t s) {
-    static int done[kMaxDevices] = {};
-    rosar_status st = ensure_smem((const void *)sparse_azimuth_kernel, SaGeo::SMEM_BYTES, done, "sparse_azimuth");
-    if (st != ROSAR_OK) return st;
-    if (n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth: n_rng=%d exceeds 65535", n_rng);
-    dim3 grid((n_az + SaGeo::TW - 1) / SaGeo::TW, n_rng);
-    sparse_azimuth_kernel<<<grid, az::THREADS, SaGeo::SMEM_BYTES, s>>>(S, w, o, o_row_stride, n_az, K, out);
-    return check_launch("sparse_azimuth");
+    return launch_gather<false>(S, w, o, o_row_stride, 1, n_rng, n_az, K, out, s);
+}
+
+rosar_status launch_sparse_azimuth_scans(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
+                                         int n_scans, int n_rng, int n_az, int K, bool adjoint, float2 *out,
+                                         cudaStream_t s) {
+    return adjoint ? launch_gather<true>(S, w, o, o_row_stride, n_scans, n_rng, n_az, K, out, s)
+                   : launch_gather<false>(S, w, o, o_row_stride, n_scans, n_rng, n_az, K, out, s);
 }
 
 }  // namespace rosar

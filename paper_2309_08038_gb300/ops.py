@@ -186,3 +186,81 @@ def image_fft(raw, win, H, workspace=None, out=None, stream=None):
     require(out, torch.complex64, "out", shape=(L, n_az))
     check(lib.rosar_image_fft(ptr(raw), ptr(win), ptr(H), n_az, L, ptr(workspace), ptr(out), stream_handle(stream)))
     return out
+
+
+# ------------------------------------------------------------------ differentiable form --
+
+def _stack(S, name):
+    require(S, torch.complex64, name, ndim=3)
+    return S.shape
+
+
+def phase_apply(S, eps, out=None, stream=None):
+    """rosar_phase_apply: S_t [n_scans, n_rng, n_az] = S * exp(j*eps[:, None, :])."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    require(eps, torch.float32, "eps", shape=(n_scans, n_az))
+    if out is None:
+        out = torch.empty_like(S)
+    require(out, torch.complex64, "S_t", shape=(n_scans, n_rng, n_az))
+    check(lib.rosar_phase_apply(ptr(S), ptr(eps), n_scans, n_rng, n_az, ptr(out), stream_handle(stream)))
+    return out
+
+
+def sparse_azimuth_scans(S, w, o, out=None, stream=None):
+    """rosar_sparse_azimuth_scans: the sparse azimuth filter of each scan of S [n_scans, n_rng, n_az]."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    require(w, torch.complex64, "w", ndim=2)
+    K = w.shape[1]
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty_like(S)
+    require(out, torch.complex64, "out", shape=(n_scans, n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_scans(ptr(S), ptr(w), ptr(o), stride, n_scans, n_rng, n_az, K, ptr(out),
+                                         stream_handle(stream)))
+    return out
+
+
+def sparse_azimuth_adjoint(g, S_t, w, o, want_S=True, want_w=True, stream=None):
+    """rosar_sparse_azimuth_adjoint: (grad_S_t or None, grad_w or None) for the image gradient g."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(g, "g")
+    require(w, torch.complex64, "w", ndim=2)
+    K = w.shape[1]
+    stride = _offsets(o, n_rng, K)
+    if want_w:
+        require(S_t, torch.complex64, "S_t", shape=(n_scans, n_rng, n_az))
+    gS = torch.empty_like(g) if want_S else None
+    gw = torch.empty_like(w) if want_w else None
+    check(lib.rosar_sparse_azimuth_adjoint(ptr(g), ptr(S_t) if want_w else None, ptr(w), ptr(o), stride, n_scans,
+                                           n_rng, n_az, K, ptr(gS), ptr(gw), stream_handle(stream)))
+    return gS, gw
+
+
+def phase_grad(S_t, grad_S_t, eps, want_eps=True, want_S=False, stream=None):
+    """rosar_phase_grad: (grad_eps [n_scans, n_az] or None, grad_S or None)."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S_t, "S_t")
+    require(grad_S_t, torch.complex64, "grad_S_t", shape=(n_scans, n_rng, n_az))
+    require(eps, torch.float32, "eps", shape=(n_scans, n_az))
+    ge = torch.empty((n_scans, n_az), dtype=torch.float32, device=S_t.device) if want_eps else None
+    gS = torch.empty_like(S_t) if want_S else None
+    check(lib.rosar_phase_grad(ptr(S_t), ptr(grad_S_t), ptr(eps), n_scans, n_rng, n_az, ptr(ge), ptr(gS),
+                               stream_handle(stream)))
+    return ge, gS
+
+
+def range_compress_adjoint(g, win=None, centred=True, out=None, stream=None):
+    """rosar_range_compress_adjoint: g [L, n_az] -> grad_raw [n_az, L]."""
+    lib = _lib.load()
+    require(g, torch.complex64, "g", ndim=2)
+    L, n_az = g.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    if out is None:
+        out = torch.empty((n_az, L), dtype=torch.complex64, device=g.device)
+    require(out, torch.complex64, "grad_raw", shape=(n_az, L))
+    check(lib.rosar_range_compress_adjoint(ptr(g), ptr(win), n_az, L, int(bool(centred)), ptr(out),
+                                           stream_handle(stream)))
+    return out

@@ -1,0 +1,185 @@
+"""Differentiable form: adjoint kernels and autograd against the FP64 oracle and finite differences (GPU).
+
+Bar: gradients within 1e-3 relative error of the FP64 reference (they land near 1e-6).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-3
+
+
+@pytest.fixture(scope="module")
+def rosar():
+    from paper_2309_08038_gb300 import build
+    build.build()
+    import paper_2309_08038_gb300 as r
+    return r
+
+
+def _c(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _cuda(torch, x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_phase_apply_and_adjoints_match_oracle(rosar):
+    import torch
+    rng = np.random.default_rng(1)
+    n_scans, n_rng, n_az, K, M = 3, 9, 1031, 40, 300
+    S = _c(rng, n_scans, n_rng, n_az)
+    eps = (rng.standard_normal((n_scans, n_az)) * 0.3).astype(np.float32)
+    w = _c(rng, n_rng, K)
+    o = (np.sort(rng.choice(M, K, replace=False)) - M // 2).astype(np.int32)
+    g = _c(rng, n_scans, n_rng, n_az)
+    S_t = rosar.phase_apply(_cuda(torch, S), _cuda(torch, eps))
+    out = rosar.sparse_azimuth_scans(S_t, _cuda(torch, w), _cuda(torch, o)).cpu().numpy()
+    gS, gw = rosar.sparse_azimuth_adjoint(_cuda(torch, g), S_t, _cuda(torch, w), _cuda(torch, o))
+    ge, gSraw = rosar.phase_grad(S_t, gS, _cuda(torch, eps), want_eps=True, want_S=True)
+    S_t = S_t.cpu().numpy()
+    ref_gw = np.zeros((n_rng, K), np.complex128)
+    for s in range(n_scans):
+        ref_t = O.apply_phase_errors(S[s], eps[s])
+        assert _rel(S_t[s], ref_t) < 1e-6
+        assert _rel(out[s], O.sparse_azimuth(ref_t, w, o)) < 1e-5
+        ref_gS = O.sparse_azimuth_adjoint_S(g[s], w, o)
+        assert _rel(gS[s].cpu().numpy(), ref_gS) < 1e-5
+        assert _rel(ge[s].cpu().numpy(), O.phase_error_grad(ref_t, ref_gS)) < 1e-5
+        assert _rel(gSraw[s].cpu().numpy(), ref_gS * np.exp(-1j * eps[s].astype(np.float64))[None, :]) < 1e-5
+        ref_gw += O.sparse_azimuth_adjoint_w(g[s], ref_t, o)
+    assert _rel(gw.cpu().numpy(), ref_gw) < 1e-5
+
+
+def test_weight_grad_wide_span_and_per_row_offsets(rosar):
+    """Offsets spanning more than the staged window (direct-gather path) and per-row offsets."""
+    import torch
+    rng = np.random.default_rng(2)
+    n_rng, n_az, K = 4, 9000, 12
+    o = np.stack([np.sort(rng.choice(np.arange(-4400, 4400), K, replace=False)) for _ in range(n_rng)]).astype(np.int32)
+    S, g, w = _c(rng, 1, n_rng, n_az), _c(rng, 1, n_rng, n_az), _c(rng, n_rng, K)
+    gS, gw = rosar.sparse_azimuth_adjoint(_cuda(torch, g), _cuda(torch, S), _cuda(torch, w), _cuda(torch, o))
+    assert _rel(gw.cpu().numpy(), O.sparse_azimuth_adjoint_w(g[0], S[0], o)) < 1e-5
+    assert _rel(gS[0].cpu().numpy(), O.sparse_azimuth_adjoint_S(g[0], w, o)) < 1e-5
+
+
+@pytest.mark.parametrize("L,n_az", [(8, 37), (64, 360), (256, 100), (1024, 33), (4096, 5)])
+def test_range_compress_adjoint_matches_oracle(rosar, L, n_az):
+    import torch
+    rng = np.random.default_rng(L)
+    g = _c(rng, L, n_az)
+    win = synth.hann_window(L)
+    for centred in (True, False):
+        got = rosar.range_compress_adjoint(_cuda(torch, g), _cuda(torch, win), centred=centred).cpu().numpy()
+        assert _rel(got, O.range_compress_adjoint(g, win, centred)) < 2e-6, (L, n_az, centred)
+
+
+def _crop_problem(seed=3):
+    """The 64-pulse crop: 64 pulses, 32 range rows, K = 16 taps of M = 32, two scans."""
+    rng = np.random.default_rng(seed)
+    n_scans, n_rng, n_az, K, M = 2, 32, 64, 16, 32
+    S = _c(rng, n_scans, n_rng, n_az)
+    B = _c(rng, n_scans, n_rng, n_az)
+    w = (_c(rng, n_rng, K) / 4).astype(np.complex64)
+    o = (np.sort(rng.choice(M, K, replace=False)) - M // 2).astype(np.int32)
+    eps = (rng.standard_normal((n_scans, n_az)) * 0.3).astype(np.float32)
+    return S, B, w, o, eps
+
+
+def _oracle_loss(S, B, w, o, eps):
+    return float(sum(np.sum(np.abs(O.sparse_azimuth(O.apply_phase_errors(S[s], eps[s]), w, o) - B[s]) ** 2)
+                     for s in range(S.shape[0])))
+
+
+def test_autograd_matches_fp64_finite_differences_on_crop(rosar):
+    import torch
+    S, B, w, o, eps = _crop_problem()
+    tS = _cuda(torch, S).requires_grad_(True)
+    te = _cuda(torch, eps).requires_grad_(True)
+    tw = _cuda(torch, w).requires_grad_(True)
+    out = rosar.autograd.sparse_azimuth_phase(tS, te, tw, _cuda(torch, o))
+    loss = torch.sum(torch.abs(out - _cuda(torch, B)) ** 2)
+    loss.backward()
+    # FP64 oracle gradients
+    ref_w = np.zeros_like(w, dtype=np.complex128)
+    ref_e = np.zeros_like(eps, dtype=np.float64)
+    ref_S = np.zeros_like(S, dtype=np.complex128)
+    for s in range(S.shape[0]):
+        St = O.apply_phase_errors(S[s], eps[s])
+        gr = 2.0 * (O.sparse_azimuth(St, w, o) - B[s])
+        G = O.sparse_azimuth_adjoint_S(gr, w, o)
+        ref_w += O.sparse_azimuth_adjoint_w(gr, St, o)
+        ref_e[s] = O.phase_error_grad(St, G)
+        ref_S[s] = G * np.exp(-1j * eps[s].astype(np.float64))[None, :]
+    assert _rel(tw.grad.cpu().numpy(), ref_w) < TOL_GRAD
+    assert _rel(te.grad.cpu().numpy(), ref_e) < TOL_GRAD
+    assert _rel(tS.grad.cpu().numpy(), ref_S) < TOL_GRAD
+    # FP64 central differences of the loss (h = 1e-6) on sampled coordinates
+    S64, B64, w64, e64 = S.astype(np.complex128), B.astype(np.complex128), w.astype(np.complex128), eps.astype(np.float64)
+    h = 1e-6
+    for (s, n) in [(0, 0), (0, 17), (1, 40), (1, 63)]:
+        ep, em = e64.copy(), e64.copy()
+        ep[s, n] += h
+        em[s, n] -= h
+        fd = (_oracle_loss(S64, B64, w64, o, ep) - _oracle_loss(S64, B64, w64, o, em)) / (2 * h)
+        assert abs(te.grad[s, n].item() - fd) <= TOL_GRAD * max(abs(fd), np.abs(ref_e).max() * 1e-2)
+    for (r, k) in [(0, 0), (5, 7), (31, 15)]:
+        fd = 0j
+        for part, dz in enumerate((1.0, 1j)):
+            wp, wm = w64.copy(), w64.copy()
+            wp[r, k] += h * dz
+            wm[r, k] -= h * dz
+            fd += (1 if part == 0 else 1j) * (_oracle_loss(S64, B64, wp, o, e64) - _oracle_loss(S64, B64, wm, o, e64)) / (2 * h)
+        assert abs(complex(tw.grad[r, k].item()) - fd) <= TOL_GRAD * max(abs(fd), np.abs(ref_w).max() * 1e-2)
+
+
+def test_range_compress_autograd(rosar):
+    import torch
+    rng = np.random.default_rng(4)
+    n_az, L = 50, 64
+    raw = _c(rng, n_az, L)
+    B = _c(rng, L, n_az)
+    win = synth.hann_window(L)
+    t = _cuda(torch, raw).requires_grad_(True)
+    S = rosar.autograd.range_compress(t, _cuda(torch, win))
+    torch.sum(torch.abs(S - _cuda(torch, B)) ** 2).backward()
+    ref = O.range_compress_adjoint(2.0 * (O.range_compress(raw, win) - B), win)
+    assert _rel(t.grad.cpu().numpy(), ref) < 1e-5
+
+
+def test_full_diff_workload_against_oracle(rosar):
+    """16 indoor-geometry scans, shared w [256, 64], eps [16, 3600]: grad w and grad eps of
+    ||image - reference||^2 in the launch configuration the benchmark times, vs the FP64 oracle."""
+    import torch
+    cfg = synth.INDOOR
+    rng = np.random.default_rng(5)
+    n_scans = 16
+    S = _c(rng, n_scans, cfg.L, cfg.n_az)
+    Bref = _c(rng, n_scans, cfg.L, cfg.n_az)
+    o = synth.draw_offsets(cfg)
+    w = synth.default_weights(cfg, o)
+    eps = (rng.standard_normal((n_scans, cfg.n_az)) * 0.3).astype(np.float32)
+    tw = _cuda(torch, w).requires_grad_(True)
+    te = _cuda(torch, eps).requires_grad_(True)
+    out = rosar.autograd.sparse_azimuth_phase(_cuda(torch, S), te, tw, _cuda(torch, o))
+    torch.sum(torch.abs(out - _cuda(torch, Bref)) ** 2).backward()
+    gw = tw.grad.cpu().numpy()
+    ge = te.grad.cpu().numpy()
+    ref_w = np.zeros((cfg.L, cfg.K), np.complex128)
+    for s in range(n_scans):
+        St = O.apply_phase_errors(S[s], eps[s])
+        gr = 2.0 * (O.sparse_azimuth(St, w, o) - Bref[s])
+        ref_w += O.sparse_azimuth_adjoint_w(gr, St, o)
+        if s in (0, 15):
+            assert _rel(ge[s], O.phase_error_grad(St, O.sparse_azimuth_adjoint_S(gr, w, o))) < TOL_GRAD
+    assert _rel(gw, ref_w) < TOL_GRAD
