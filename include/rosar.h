@@ -238,7 +238,8 @@ ROSAR_API rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const fl
  * ticket than any of its azimuth tiles, so the tiles a wait depends on are
  * already owned by running CTAs and the wait ends; it is nevertheless bounded
  * (spin_limit polls), after which the kernel records ROSAR_ERR_TIMEOUT and
- * every CTA returns.  Results equal rosar_image scan by scan.
+ * every CTA returns.  Results equal rosar_image (or rosar_image_fft, for a scan
+ * given its plan H) scan by scan, bit for bit.
  * ------------------------------------------------------------------------ */
 typedef struct rosar_scan {
     const rosar_c32 *raw;   /* [n_az][L] complex input                                  (in) */
@@ -251,6 +252,10 @@ typedef struct rosar_scan {
     int K;                  /* >= 1 */
     rosar_c32 *S;           /* [L][n_az] workspace: range-compressed data          (scratch) */
     rosar_c32 *out;         /* [L][n_az] image                                          (out) */
+    const rosar_c32 *H;     /* [L][n_az] plan from rosar_azimuth_plan for this scan's w, o: its
+                               azimuth filter runs as whole-row FFT tiles (as rosar_image_fft);
+                               NULL: gather tiles (as rosar_image).  n_az must then satisfy
+                               rosar_azimuth_fft_supported.                             (in) */
 } rosar_scan;
 
 typedef struct rosar_batch_tuning {

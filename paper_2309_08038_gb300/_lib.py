@@ -33,7 +33,7 @@ class RadarStruct(ctypes.Structure):
 class ScanStruct(ctypes.Structure):
     _fields_ = [("raw", ctypes.c_void_p), ("win", ctypes.c_void_p), ("w", ctypes.c_void_p), ("o", ctypes.c_void_p),
                 ("o_row_stride", ctypes.c_int), ("n_az", ctypes.c_int), ("L", ctypes.c_int), ("K", ctypes.c_int),
-                ("S", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("S", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_void_p)]
 
 
 class BatchTuningStruct(ctypes.Structure):

@@ -31,7 +31,8 @@ class Batch:
     """A set of scans bound to one CUDA graph [counter reset -> persistent kernel].
 
     Each scan is a dict with CUDA tensors raw [n_az, L], w [L, K], o [K] or [L, K], and optionally
-    win [L], S [L, n_az] (workspace) and out [L, n_az] (allocated here when missing).  The tensors are
+    win [L], S [L, n_az] (workspace), out [L, n_az] (allocated here when missing) and H [L, n_az]
+    (the scan's plan from azimuth_plan: its azimuth filter then runs as whole-row FFT tiles).  The tensors are
     referenced for the lifetime of the batch; `launch()` re-reads whatever they hold.
     """
 
@@ -58,9 +59,13 @@ class Batch:
                 out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
             require(S, torch.complex64, f"scans[{i}].S", shape=(L, n_az))
             require(out, torch.complex64, f"scans[{i}].out", shape=(L, n_az))
+            H = sc.get("H")
+            if H is not None:
+                require(H, torch.complex64, f"scans[{i}].H", shape=(L, n_az))
             arr[i] = _lib.ScanStruct(raw.data_ptr(), win.data_ptr() if win is not None else None, w.data_ptr(),
-                                     o.data_ptr(), stride, n_az, L, K, S.data_ptr(), out.data_ptr())
-            self._keep += [raw, w, o, win, S, out]
+                                     o.data_ptr(), stride, n_az, L, K, S.data_ptr(), out.data_ptr(),
+                                     H.data_ptr() if H is not None else None)
+            self._keep += [raw, w, o, win, S, out, H]
             self.outs.append(out)
         nbytes = lib.rosar_batch_workspace_bytes(len(scans))
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.outs[0].device)

@@ -3,7 +3,8 @@
 // Work is a list of tiles in ticket order.  A range tile runs the range-FFT tile
 // (fft_tile.cuh) on P = 4096/L pulses of one scan with the CTA's 256 threads; an
 // azimuth tile runs the gather-MAC tile (azimuth_tile.cuh) on 256*J outputs of one
-// row of one scan.  Tickets are handed out by an atomic counter, range tiles of a
+// row of one scan, or, for a scan given its frequency-domain plan H, the whole row
+// through the row FFT (row_fft.cuh): forward transform, product with H, inverse.  Tickets are handed out by an atomic counter, range tiles of a
 // scan always before its azimuth tiles; the scan's done-counter is bumped (release)
 // after each range tile, and an azimuth tile's thread 0 polls it (acquire) before
 // the CTA reads S through L2.  The poll is bounded; on expiry the kernel raises an
@@ -16,6 +17,7 @@
 
 #include "azimuth_tile.cuh"
 #include "fft_tile.cuh"
+#include "row_fft.cuh"
 
 namespace rosar {
 namespace {
@@ -29,8 +31,10 @@ struct ScanDev {
     const int32_t *o;
     float2 *S;
     float2 *out;
+    const float2 *H;          // frequency-domain plan [L][n_az], or null: gather tiles
     int o_row_stride, n_az, L, K;
     int range_tiles, az_tiles_per_row, P, vec_store;
+    rowfft::RowPlan plan;
 };
 
 struct Segment {
@@ -59,6 +63,45 @@ template <int L>
 __device__ __forceinline__ void run_range(const ScanDev &sc, int n0, char *sm, bool build) {
     fft::range_tile<L, 4096 / L>(sc.raw, sc.win, sc.n_az, true, sc.S, n0, reinterpret_cast<float2 *>(sm), build,
                                  sc.vec_store != 0);
+}
+
+// One range row of a scan through the frequency-domain azimuth filter (same arithmetic as
+// rosar_sparse_azimuth_fft).  S was written by this kernel's range tiles: read through L2 (ld.cg),
+// eight loads in flight per thread.
+__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem) {
+    const int N = sc.n_az;
+    float2 *x = reinterpret_cast<float2 *>(smem);
+    float2 *tw = x + rowfft::padded_len(N);
+    const float2 *tc, *tf;
+    rowfft::build_twiddles(N, false, tw, &tc, &tf);
+    const size_t row = (size_t)r * N;
+    const float2 *Srow = sc.S + row;
+    for (int n0 = threadIdx.x; n0 < N; n0 += 8 * BT_THREADS) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int n = n0 + u * BT_THREADS;
+            v[u] = n < N ? __ldcg(Srow + n) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int n = n0 + u * BT_THREADS;
+            if (n < N) x[rowfft::pad16(n)] = v[u];
+        }
+    }
+    __syncthreads();
+    rowfft::row_dif(x, N, sc.plan, tc, tf);
+    for (int n = threadIdx.x; n < N; n += BT_THREADS) {
+        const float2 y = cmul(__ldg(sc.H + row + n), x[rowfft::pad16(n)]);
+        x[rowfft::pad16(n)] = make_float2(y.x, -y.y);
+    }
+    __syncthreads();
+    rowfft::row_dit(x, N, sc.plan, tc, tf);
+    for (int n = threadIdx.x; n < N; n += BT_THREADS) {
+        const float2 y = x[rowfft::pad16(n)];
+        sc.out[row + n] = make_float2(y.x, -y.y);
+    }
+    __syncthreads();
 }
 
 template <int J>
@@ -122,9 +165,13 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
             }
             __syncthreads();
             if (s_abort) break;
-            const int r = local / sc.az_tiles_per_row;
-            const int th0 = (local - r * sc.az_tiles_per_row) * az::Geo<J>::TW;
-            az::azimuth_tile<J, true>(sc.S, sc.w, sc.o, sc.o_row_stride, sc.n_az, sc.K, sc.out, r, th0, sm, red);
+            if (sc.H) {
+                fft_row_tile(sc, local, sm);
+            } else {
+                const int r = local / sc.az_tiles_per_row;
+                const int th0 = (local - r * sc.az_tiles_per_row) * az::Geo<J>::TW;
+                az::azimuth_tile<J, true>(sc.S, sc.w, sc.o, sc.o_row_stride, sc.n_az, sc.K, sc.out, r, th0, sm, red);
+            }
         }
     }
 }
@@ -235,15 +282,25 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
         d.o = q.o;
         d.S = reinterpret_cast<float2 *>(q.S);
         d.out = reinterpret_cast<float2 *>(q.out);
+        d.H = reinterpret_cast<const float2 *>(q.H);
+        if (q.H && !rowfft::make_plan(q.n_az, &d.plan)) {
+            st = set_error(ROSAR_ERR_UNSUPPORTED, "batch_create: scan %d: n_az=%d has no frequency-domain plan", s,
+                           q.n_az);
+            break;
+        }
         d.o_row_stride = q.o_row_stride;
         d.n_az = q.n_az;
         d.L = q.L;
         d.K = q.K;
         d.P = 4096 / q.L;
         d.range_tiles = (q.n_az + d.P - 1) / d.P;
-        d.az_tiles_per_row = (q.n_az + tn.az_tile - 1) / tn.az_tile;
+        d.az_tiles_per_row = q.H ? 1 : (q.n_az + tn.az_tile - 1) / tn.az_tile;
         d.vec_store = (q.n_az % 2 == 0) && (reinterpret_cast<uintptr_t>(q.S) % 16 == 0);
         smem = smem > range_smem_bytes(q.L) ? smem : range_smem_bytes(q.L);
+        if (q.H) {
+            const int rs = (int)(sizeof(float2) * (size_t)(rowfft::padded_len(q.n_az) + 64 + rowfft::coarse_len(q.n_az)));
+            smem = smem > rs ? smem : rs;
+        }
         total_range += d.range_tiles;
         total_az += (long long)d.az_tiles_per_row * q.L;
     }

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/rosar.h"
+#include "rosar.h"
 
 namespace rosar {
 

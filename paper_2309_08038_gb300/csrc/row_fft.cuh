@@ -1,0 +1,292 @@
+// Mixed-radix row FFT used by the frequency-domain azimuth filter (azimuth_fft.cu) and by
+// the batched persistent kernel (batch.cu): in-place decimation-in-frequency forward
+// transform (digit-reversed output) and its transposed decimation-in-time sequence.
+// All functions run on the whole CTA (blockDim.x threads, any count) and end with a barrier.
+#pragma once
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "fft_tile.cuh"
+
+namespace rosar {
+namespace rowfft {
+
+
+constexpr int AF_MAX_N = 16384;
+constexpr int AF_MAXPASS = 16;
+
+struct RowPlan {
+    int npass;
+    int rad[AF_MAXPASS];
+};
+
+__host__ __device__ constexpr int padded_len(int n) { return n + n / 16 + 1; }
+__host__ __device__ constexpr int coarse_len(int n) { return n / 64 + 1; }
+
+// Forward DFT of size R on v[0..R), natural-order output.
+template <int R>
+__device__ __forceinline__ void small_dft(float2 *v);
+
+template <>
+__device__ __forceinline__ void small_dft<2>(float2 *v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<3>(float2 *v) {
+    constexpr float h = 0.86602540378443865f;   // sin(2*pi/3)
+    const float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    const float2 y0 = cadd(v[0], t1);
+    const float2 a = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+    const float2 b = make_float2(h * t2.x, h * t2.y);           // y1 = a - i b, y2 = a + i b
+    v[0] = y0;
+    v[1] = make_float2(a.x + b.y, a.y - b.x);
+    v[2] = make_float2(a.x - b.y, a.y + b.x);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<4>(float2 *v) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);          // d02 - i d13
+    v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);          // d02 + i d13
+}
+
+template <>
+__device__ __forceinline__ void small_dft<5>(float2 *v) {
+    constexpr float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos(2pi/5), cos(4pi/5)
+    constexpr float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;    // sin(2pi/5), sin(4pi/5)
+    const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    const float2 x0 = v[0];
+    const float2 a1 = make_float2(fmaf(c1, t1.x, fmaf(c2, t2.x, x0.x)), fmaf(c1, t1.y, fmaf(c2, t2.y, x0.y)));
+    const float2 a2 = make_float2(fmaf(c2, t1.x, fmaf(c1, t2.x, x0.x)), fmaf(c2, t1.y, fmaf(c1, t2.y, x0.y)));
+    const float2 b1 = make_float2(fmaf(s1, t3.x, s2 * t4.x), fmaf(s1, t3.y, s2 * t4.y));
+    const float2 b2 = make_float2(fmaf(s2, t3.x, -s1 * t4.x), fmaf(s2, t3.y, -s1 * t4.y));
+    v[0] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+    v[1] = make_float2(a1.x + b1.y, a1.y - b1.x);              // a1 - i b1
+    v[4] = make_float2(a1.x - b1.y, a1.y + b1.x);              // a1 + i b1
+    v[2] = make_float2(a2.x + b2.y, a2.y - b2.x);              // a2 - i b2
+    v[3] = make_float2(a2.x - b2.y, a2.y + b2.x);              // a2 + i b2
+}
+
+template <int R>
+__device__ __forceinline__ void pow2_dft(float2 *v) {
+    fft::dft_dif<R>(v);                     // output index r sits at v[brev(r)]
+    float2 t[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) t[r] = v[fft::brev(r, fft::ilog2(R))];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = t[r];
+}
+
+template <>
+__device__ __forceinline__ void small_dft<8>(float2 *v) { pow2_dft<8>(v); }
+
+template <>
+__device__ __forceinline__ void small_dft<16>(float2 *v) { pow2_dft<16>(v); }
+
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
+// floor(i / s) for 0 <= i < 2^23 and 1 <= s <= 2^14, from inv_s = 1/s rounded to float: (i + 1/2)/s is at
+// least 1/(2s) away from an integer while the float product errs by at most about i * 2^-23 / s.
+__device__ __forceinline__ int quot(int i, float inv_s) { return __float2int_rz(__fmul_rn((float)i + 0.5f, inv_s)); }
+
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory"); }
+
+// exp(-2*pi*i*q/N), 0 <= q < N: from the full table (tc == nullptr: tf holds all N entries) or from
+// the coarse (q >> 6) and fine (q & 63) tables.
+__device__ __forceinline__ float2 twiddle(int q, const float2 *tc, const float2 *tf) {
+    return tc ? cmul(tc[q >> 6], tf[q & 63]) : tf[q];
+}
+
+// wq[q] = w1^q for q = 1..R-1 by repeated squaring and products (depth <= 4 multiplications, so the
+// rounding error stays within a few ulp).  One table load per butterfly (w1 = W^(j*tstep), consecutive
+// across threads, hence conflict-free) replaces R-1 scattered loads.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w1, float2 (&wq)[R]) {
+    wq[0] = make_float2(1.f, 0.f);
+    if (R > 1) wq[1] = w1;
+#pragma unroll
+    for (int q = 2; q < R; ++q) wq[q] = (q & 1) ? cmul(wq[q - 1], w1) : cmul(wq[q / 2], wq[q / 2]);
+}
+
+// One in-place decimation-in-frequency stage: radix R on blocks of length M (stride s = M/R):
+// v = DFT_R(x[base + r*s]); x[base + q*s] = v[q] * W_M^(j*q).
+template <int R>
+__device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
+    const int s = M / R, tstep = N / M, nb = N / R;
+    const float inv_s = 1.f / (float)s;
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int blk = quot(idx, inv_s), j = idx - blk * s;
+        const int base = blk * M + j;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[pad16(base + r * s)];
+        small_dft<R>(v);
+        x[pad16(base)] = v[0];
+        float2 wq[R];
+        twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[pad16(base + q * s)] = cmul(v[q], wq[q]);
+    }
+    __syncthreads();
+}
+
+// The transposed stage (decimation in time): v[q] = x[base + q*s] * W_M^(j*q); x[base + r*s] = DFT_R(v)[r].
+template <int R>
+__device__ __forceinline__ void dit_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
+    const int s = M / R, tstep = N / M, nb = N / R;
+    const float inv_s = 1.f / (float)s;
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int blk = quot(idx, inv_s), j = idx - blk * s;
+        const int base = blk * M + j;
+        float2 v[R];
+        float2 wq[R];
+        twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
+        v[0] = x[pad16(base)];
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmul(x[pad16(base + q * s)], wq[q]);
+        small_dft<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[pad16(base + r * s)] = v[r];
+    }
+    __syncthreads();
+}
+
+#define ROSAR_STAGE_CASE(RR) \
+    case RR: DIF ? dif_pass<RR>(x, N, M, tc, tf) : dit_pass<RR>(x, N, M, tc, tf); break;
+
+template <bool DIF>
+__device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
+    switch (R) {
+        ROSAR_STAGE_CASE(16)
+        ROSAR_STAGE_CASE(8)
+        ROSAR_STAGE_CASE(5)
+        ROSAR_STAGE_CASE(4)
+        ROSAR_STAGE_CASE(3)
+        default: DIF ? dif_pass<2>(x, N, M, tc, tf) : dit_pass<2>(x, N, M, tc, tf); break;
+    }
+}
+#undef ROSAR_STAGE_CASE
+
+// Forward DFT of the row, output in digit-reversed order.
+__device__ __forceinline__ void row_dif(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+    int M = N;
+    for (int p = 0; p < pl.npass; ++p) {
+        stage<true>(pl.rad[p], x, N, M, tc, tf);
+        M /= pl.rad[p];
+    }
+}
+
+// Forward DFT of a row held in digit-reversed order, output in natural order.
+__device__ __forceinline__ void row_dit(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+    int M = 1;
+    for (int p = pl.npass - 1; p >= 0; --p) {
+        M *= pl.rad[p];
+        stage<false>(pl.rad[p], x, N, M, tc, tf);
+    }
+}
+
+// Full table (tc == nullptr on return): tw[q] = exp(-2*pi*i*q/N), q < N.  Two-level: tw[0..64) fine, then coarse.
+__device__ __forceinline__ void build_twiddles(int N, bool full, float2 *tw, const float2 **tc, const float2 **tf) {
+    if (full) {
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            float s, c;
+            sincospif(2.f * (float)q / (float)N, &s, &c);
+            tw[q] = make_float2(c, -s);
+        }
+        *tc = nullptr;
+        *tf = tw;
+        return;
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        float s, c;
+        sincospif(2.f * (float)i / (float)N, &s, &c);
+        tw[i] = make_float2(c, -s);
+    }
+    for (int i = threadIdx.x; i < coarse_len(N); i += blockDim.x) {
+        float s, c;
+        sincospif(2.f * (float)(64 * i) / (float)N, &s, &c);
+        tw[64 + i] = make_float2(c, -s);
+    }
+    *tc = tw + 64;
+    *tf = tw;
+}
+
+
+inline int threads_for(int N) { return N <= 4096 ? 256 : N <= 8192 ? 512 : 1024; }
+
+// Radix sequence for N over radices {16, 8, 4, 2, 5, 3}: fewest passes, then fewest butterflies per thread.
+// (Larger composite radices 6..15 shorten the sequence but lengthen each thread's serial chain; with the
+// few warps one row per CTA leaves per SM they measured slower on the 3600-pulse rows.)
+inline bool make_plan(int N, RowPlan *pl) {
+    static const int kRad[] = {16, 8, 4, 2, 5, 3};
+    if (N < 2 || N > AF_MAX_N) return false;
+    static std::mutex mu;
+    static std::map<int, RowPlan> cache;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(N);
+        if (it != cache.end()) {
+            *pl = it->second;
+            return pl->npass > 0;
+        }
+    }
+    const int T = threads_for(N);
+    // dynamic programme over the divisors m of N: best[m] = (passes, iterations) to transform the remaining factor m
+    std::map<int, std::pair<std::pair<int, int>, int>> best;   // m -> ((passes, iters), first radix)
+    std::vector<int> divs;
+    for (int d = 1; d <= N; ++d)
+        if (N % d == 0) divs.push_back(d);
+    best[1] = {{0, 0}, 0};
+    for (int m : divs) {
+        if (m == 1) continue;
+        std::pair<int, int> b = {1 << 30, 1 << 30};
+        int br = 0;
+        for (int R : kRad) {
+            if (m % R) continue;
+            auto it = best.find(m / R);
+            if (it == best.end() || it->second.first.first >= (1 << 30)) continue;
+            const int iters = (N / R + T - 1) / T;
+            std::pair<int, int> c = {it->second.first.first + 1, it->second.first.second + iters};
+            if (c < b) {
+                b = c;
+                br = R;
+            }
+        }
+        best[m] = {b, br};
+    }
+    RowPlan p{};
+    int m = N, np = 0;
+    bool ok = best[N].second != 0;
+    while (ok && m > 1 && np < AF_MAXPASS) {
+        const int R = best[m].second;
+        if (R == 0) { ok = false; break; }
+        p.rad[np++] = R;
+        m /= R;
+    }
+    p.npass = (ok && m == 1) ? np : 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[N] = p;
+    }
+    *pl = p;
+    return p.npass > 0;
+}
+
+
+}  // namespace rowfft
+}  // namespace rosar

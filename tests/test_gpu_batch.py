@@ -139,3 +139,52 @@ def test_full_batched_workload_matches_per_scan(rosar):
         ref = rosar.image(s["raw"], s["win"], s["w"], s["o"])
         assert torch.equal(b.outs[i], ref), i
     b.close()
+
+
+def test_batch_with_fft_plans_equals_image_fft(rosar):
+    """Scans given their frequency-domain plan run whole-row FFT azimuth tiles: bit-exact vs
+    rosar_image_fft scan by scan (the others keep gather tiles, bit-exact vs rosar_image)."""
+    import torch
+    scans, host = _make_scans(torch, seed=4)
+    ref = []
+    for i, s in enumerate(scans):
+        n_az = s["raw"].shape[0]
+        if rosar.azimuth_fft_supported(n_az) and i % 2 == 0:
+            s["H"] = rosar.azimuth_plan(s["w"], s["o"], n_az)
+            ref.append(rosar.image_fft(s["raw"], s["win"], s["H"]).cpu().numpy())
+        else:
+            ref.append(rosar.image(s["raw"], s["win"], s["w"], s["o"]).cpu().numpy())
+    assert sum("H" in s for s in scans) >= 3
+    for tuning in (rosar.Tuning(), rosar.Tuning(interleave=1, az_tile=512)):
+        b = rosar.Batch(scans, tuning)
+        b.launch()
+        b.status()
+        for i, (out, r) in enumerate(zip(b.outs, ref)):
+            assert np.array_equal(out.cpu().numpy(), r), i
+        b.close()
+    raw, w, o, win = host[0]
+    orc = O.sparse_azimuth(O.range_compress(raw, win), w, o)
+    assert np.linalg.norm(ref[0] - orc) / np.linalg.norm(orc) < 1e-4
+
+
+def test_full_batched_workload_with_plans(rosar):
+    import torch
+    cfgs = synth.batched_configs()
+    rng = np.random.default_rng(6)
+    cubes = {}
+    scans = []
+    for c in cfgs:
+        key = (c.n_az, c.L)
+        if key not in cubes:
+            cubes[key] = torch.from_numpy(_crand(rng, c.n_az, c.L)).cuda()
+        o = torch.from_numpy(synth.draw_offsets(c)).cuda()
+        w = torch.from_numpy(synth.default_weights(c, synth.draw_offsets(c))).cuda()
+        scans.append({"raw": cubes[key].clone(), "w": w, "o": o, "H": rosar.azimuth_plan(w, o, c.n_az),
+                      "win": torch.from_numpy(synth.hann_window(c.L)).cuda()})
+    b = rosar.Batch(scans)
+    b.launch()
+    b.status()
+    for i in range(0, len(scans), 23):
+        s = scans[i]
+        assert torch.equal(b.outs[i], rosar.image_fft(s["raw"], s["win"], s["H"])), i
+    b.close()
