@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-scan batched comparison")
     ap.add_argument("--gather", action="store_true", help="time the gather-MAC azimuth path instead of the FFT form")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-form comparison")
+    ap.add_argument("--batch-scans", type=int, default=256, help="scans in the batched comparison (a prefix of the 256)")
     return ap.parse_args()
 
 
@@ -174,12 +175,12 @@ def indoor_inputs(torch, device, rank):
         torch.from_numpy(win).to(device)
 
 
-def batched_inputs(torch, device):
-    """The 256-scan batched workload: one seeded scene cube per (n_az, L) pair, copied into each scan's
-    own buffer; per-scan sparse offsets and default weights."""
+def batched_inputs(torch, device, n_scans=256):
+    """The 256-scan batched workload (or its first n_scans scans): one seeded scene cube per (n_az, L)
+    pair, copied into each scan's own buffer; per-scan sparse offsets and default weights."""
     import numpy as np
     import synth
-    cfgs = synth.batched_configs()
+    cfgs = synth.batched_configs()[:n_scans]
     cubes = {}
     scans = []
     for c in cfgs:
@@ -365,8 +366,10 @@ def run_ours(args):
     outs = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(N_BUF)]
     assert N_BUF * 3 * px * 8 > 2 * L2_BYTES
 
-    # the frequency-domain plan of the weight design: computed once, outside the timed region
-    fft_ok = rosar.azimuth_fft_supported(cfg.n_az) and not args.gather
+    # azimuth path picked by the autotuner (timed on this GPU, cached); the frequency-domain plan
+    # of the weight design is computed once, outside the timed region
+    choice = rosar.autotune.choose_azimuth(cfg.L, cfg.n_az, cfg.K)
+    fft_ok = choice["path"] == "fft" and not args.gather
     H = None
     t_plan = None
     if fft_ok:
@@ -426,7 +429,8 @@ def run_ours(args):
         kernels["azimuth_fft_kernel<256>"] = {
             "us_per_launch": t_k2f * 1e6, "algorithmic_bytes": k2f_bytes, "gbs": k2f_bytes / t_k2f / 1e9,
             "hbm_frac": k2f_bytes / t_k2f / 1e9 / hbm,
-            "traffic": recorded_traffic("azimuth_fft_kernel<256>", "indoor", source_hash("azimuth_fft.cu")),
+            "traffic": recorded_traffic("azimuth_fft_kernel<256>", "indoor",
+                                        source_hash("azimuth_fft.cu", "row_fft.cuh", "fft_tile.cuh")),
             "plan_us_once": t_plan * 1e6}
     if fft_ok:
         dom_name = "azimuth_fft_kernel<256>" if t_k2f >= t_k1 else "range_compress_kernel<256>"
@@ -444,7 +448,7 @@ def run_ours(args):
                                  f"(sm_max_mhz of {peak_src} peaks)",
                     "algorithmic_flops": k2_flops, "us_per_launch": t_k2 * 1e6}
     paths = {"image_fft_px_s": value if fft_ok else None, "image_gather_px_s": world * px / t_gather_img,
-             "timed_path": "rosar_image_fft" if fft_ok else "rosar_image"}
+             "timed_path": "rosar_image_fft" if fft_ok else "rosar_image", "autotune": choice}
 
     # end to end through the public API with pinned host buffers
     hraw = [r.cpu().pin_memory() for r in raws[:4]]
@@ -491,7 +495,7 @@ def run_ours(args):
 
     batched = {}
     if not args.no_batched:
-        cfgs, bscans = batched_inputs(torch, device)
+        cfgs, bscans = batched_inputs(torch, device, args.batch_scans)
         px_b = sum(c.L * c.n_az for c in cfgs)
         nb = 10
         g = rosar.Batch(bscans)                        # gather-MAC azimuth tiles
@@ -502,7 +506,8 @@ def run_ours(args):
         info_g = g.info()
         g.close()
         attach_plans(rosar, bscans)
-        b = rosar.Batch(bscans)                        # whole-row FFT azimuth tiles
+        tuned = rosar.autotune.tune_batch(bscans)
+        b = rosar.Batch(bscans, tuned["tuning"])       # whole-row FFT azimuth tiles, autotuned tiling
         b.launch()
         b.status()
         ms_b, _ = time_loop(torch, lambda i: b.launch(stream), nb, 2, stream, world, device)
@@ -528,6 +533,7 @@ def run_ours(args):
                    "speedup_vs_plain": t_p / t_b, "speedup_vs_plain_fft": t_pf / t_b,
                    "hbm_gbs_16B_per_px": 16.0 * px_b / t_b / 1e9, "hbm_frac_16B_per_px": 16.0 * px_b / t_b / 1e9 / hbm,
                    "tiles": info, "tiles_gather": info_g, "tuning": vars(b.tuning),
+                   "autotune_ms": tuned["ms"], "autotune_cached": tuned.get("cached", False),
                    "note": "one persistent graph-captured launch (whole-row FFT azimuth tiles with per-scan plans; "
                            "gather tiles for the record) vs 256 rosar_image / rosar_image_fft calls (512 launches); "
                            "16 B/px = raw read + image write, the two-pass minimum is 32 B/px"}

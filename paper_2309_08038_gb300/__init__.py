@@ -11,6 +11,6 @@ from .ops import (Radar, azimuth_fft_supported, azimuth_plan, bpa, image, image_
 from .ops import (phase_apply, phase_grad, range_compress_adjoint, sparse_azimuth_adjoint,  # noqa: F401
                   sparse_azimuth_scans)
 from .batch import Batch, Tuning  # noqa: F401
-from . import autograd  # noqa: F401
+from . import autograd, autotune  # noqa: F401
 
 __version__ = "0.1.0"
