@@ -44,18 +44,18 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
     float2 *hb = x + padded_len(N);
     float2 *tw = lay.stage_h ? hb + padded_len(N) : hb;
     const size_t row = (size_t)blockIdx.x * N;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + pad16(n), S + row + n);
-    cp_async_commit();
+    // prologue independent of S: the H row and the twiddle table
     if (lay.stage_h)
         for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + pad16(n), H + row + n);
     cp_async_commit();
     const float2 *tc, *tf;
     build_twiddles(N, lay.full_tab != 0, tw, &tc, &tf);
-    cp_async_wait<1>();
-    __syncthreads();
-    row_dif(x, N, pl, tc, tf);
+    griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + pad16(n), S + row + n);
+    cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
+    row_dif(x, N, pl, tc, tf);
     if (lay.stage_h) {
         for (int n = threadIdx.x; n < N; n += blockDim.x) {   // spectrum times H (same digit-reversed order, carries 1/N), conjugated
             const float2 y = cmul(hb[pad16(n)], x[pad16(n)]);
@@ -133,19 +133,41 @@ int azimuth_fft_supported(int n_az) {
     return make_plan(n_az, &pl) ? 1 : 0;
 }
 
-rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s) {
+template <int MAXT>
+cudaError_t launch_fft_rows(int g, int t, size_t sm, cudaStream_t s, bool overlap, const float2 *S, const float2 *H,
+                            int N, const RowPlan &pl, const Layout &lay, float2 *out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(t);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, azimuth_fft_kernel<MAXT>, S, H, N, pl, lay, out);
+}
+
+rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
+                                bool overlap_predecessor) {
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
     static int done[3][kMaxDevices] = {};
     const Layout lay = layout_for(n_az, true);
-    return launch_rows(
+    const bool ov = overlap_predecessor;
+    cudaError_t le = cudaSuccess;
+    rosar_status st = launch_rows(
         n_az, n_rng, lay.bytes,
-        [&](int g, int t, size_t sm) { azimuth_fft_kernel<256><<<g, t, sm, s>>>(S, H, n_az, pl, lay, out); },
-        [&](int g, int t, size_t sm) { azimuth_fft_kernel<512><<<g, t, sm, s>>>(S, H, n_az, pl, lay, out); },
-        [&](int g, int t, size_t sm) { azimuth_fft_kernel<1024><<<g, t, sm, s>>>(S, H, n_az, pl, lay, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<256>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<512>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<1024>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
         (const void *)azimuth_fft_kernel<256>, (const void *)azimuth_fft_kernel<512>,
         (const void *)azimuth_fft_kernel<1024>, done, "azimuth_fft");
+    if (st == ROSAR_OK && le != cudaSuccess)
+        return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(le));
+    return st;
 }
 
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,

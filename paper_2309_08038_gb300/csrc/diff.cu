@@ -60,32 +60,40 @@ phase_grad_kernel(const float2 *__restrict__ S_t, const float2 *__restrict__ G, 
     if (grad_eps) grad_eps[(size_t)s * n_az + n] = acc;
 }
 
-// grad_w: one CTA per range row; warp q owns taps q, q+8, q+16, ... (up to WT per pass over the data).
-// Azimuth is processed in chunks of DG_CHUNK outputs: the gradient chunk and the circular window of
-// S_t it meets are staged in shared memory; each lane accumulates its strided share of theta for
-// every tap it owns, then the warp reduces in a fixed shuffle order.
-constexpr int DG_WARPS = DG_THREADS / 32;
-constexpr int DG_WT = 16;                       // taps per warp per sweep
-constexpr int DG_CHUNK = 1024;
-constexpr int DG_SPAN_CAP = 2560;
+// grad_w: one CTA of 1024 threads per range row.  Its 32 warps form TAPG tap groups x THG azimuth
+// groups: warp (tg, hg) owns taps k0 + tg + TAPG*t (t < WT) and the azimuth positions of the current
+// chunk with (theta - t0) / (CHUNK/THG) == hg.  Azimuth is processed in chunks of CHUNK outputs: the
+// gradient chunk and the circular window of S_t it meets are staged in shared memory; lanes stride
+// their group's positions, accumulate g * conj(S_t) per tap, reduce across lanes by shuffles and then
+// across the azimuth groups in a fixed order, so results are bit-reproducible.
+constexpr int WG_THREADS = 1024;
+constexpr int WG_WARPS = WG_THREADS / 32;
+constexpr int WG_TAPG = 4;                       // tap groups
+constexpr int WG_THG = WG_WARPS / WG_TAPG;       // azimuth groups (8)
+constexpr int WG_WT = 16;                        // taps per warp per sweep
+constexpr int WG_SWEEP = WG_TAPG * WG_WT;        // 64 taps per sweep
+constexpr int WG_CHUNK = 1024;
+constexpr int WG_SPAN_CAP = 2560;
 
 __device__ __forceinline__ int canon(int o, int n) {
     int c = pmod(o, n);
     return (c > n / 2) ? c - n : c;
 }
 
-__global__ void __launch_bounds__(DG_THREADS)
+__global__ void __launch_bounds__(WG_THREADS, 1)
 weight_grad_kernel(const float2 *__restrict__ g, const float2 *__restrict__ S_t, const int32_t *__restrict__ o,
                    int o_row_stride, int n_scans, int n_rng, int n_az, int K, float2 *__restrict__ grad_w) {
-    __shared__ float2 gs[DG_CHUNK];
-    __shared__ float2 ws[DG_CHUNK + DG_SPAN_CAP];
-    __shared__ int red_lo[DG_WARPS], red_hi[DG_WARPS];
+    __shared__ float2 gs[WG_CHUNK];
+    __shared__ float2 ws[WG_CHUNK + WG_SPAN_CAP];
+    __shared__ float2 part[WG_THG][WG_SWEEP];
+    __shared__ int red_lo[WG_WARPS], red_hi[WG_WARPS];
     const int r = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tg = warp % WG_TAPG, hg = warp / WG_TAPG;
     const int32_t *orow = o + (size_t)r * o_row_stride;
 
     int lo = INT_MAX, hi = INT_MIN;
-    for (int k = threadIdx.x; k < K; k += DG_THREADS) {
+    for (int k = threadIdx.x; k < K; k += WG_THREADS) {
         const int c = canon(__ldg(orow + k), n_az);
         lo = min(lo, c);
         hi = max(hi, c);
@@ -102,44 +110,45 @@ weight_grad_kernel(const float2 *__restrict__ g, const float2 *__restrict__ S_t,
     __syncthreads();
     lo = red_lo[0];
     hi = red_hi[0];
-#pragma unroll
-    for (int i = 1; i < DG_WARPS; ++i) {
+    for (int i = 1; i < WG_WARPS; ++i) {
         lo = min(lo, red_lo[i]);
         hi = max(hi, red_hi[i]);
     }
-    const bool staged = hi - lo <= DG_SPAN_CAP;
+    const bool staged = hi - lo <= WG_SPAN_CAP;
+    constexpr int PER_G = WG_CHUNK / WG_THG;     // positions per azimuth group per chunk (128)
 
-    for (int k0 = 0; k0 < K; k0 += DG_WARPS * DG_WT) {
-        int rel[DG_WT];
-        float2 acc[DG_WT];
+    for (int k0 = 0; k0 < K; k0 += WG_SWEEP) {
+        int rel[WG_WT];
+        float2 acc[WG_WT];
 #pragma unroll
-        for (int t = 0; t < DG_WT; ++t) {
-            const int k = k0 + warp + t * DG_WARPS;
+        for (int t = 0; t < WG_WT; ++t) {
+            const int k = k0 + tg + WG_TAPG * t;
             const int c = k < K ? canon(__ldg(orow + k), n_az) : lo;
             rel[t] = staged ? c - lo : c;
             acc[t] = make_float2(0.f, 0.f);
         }
-        for (int s = 0; s < n_scans; ++s) {
-            const size_t rowoff = ((size_t)s * n_rng + r) * n_az;
+        for (int sc = 0; sc < n_scans; ++sc) {
+            const size_t rowoff = ((size_t)sc * n_rng + r) * n_az;
             const float2 *grow = g + rowoff;
             const float2 *srow = S_t + rowoff;
-            for (int t0 = 0; t0 < n_az; t0 += DG_CHUNK) {
-                const int cw = min(DG_CHUNK, n_az - t0);
+            for (int t0 = 0; t0 < n_az; t0 += WG_CHUNK) {
+                const int cw = min(WG_CHUNK, n_az - t0);
                 __syncthreads();
-                for (int i = threadIdx.x; i < cw; i += DG_THREADS) gs[i] = __ldg(grow + t0 + i);
+                for (int i = threadIdx.x; i < cw; i += WG_THREADS) gs[i] = __ldg(grow + t0 + i);
                 if (staged) {
                     const int start = pmod(t0 + lo, n_az);
-                    for (int i = threadIdx.x; i < cw + hi - lo; i += DG_THREADS) {
+                    for (int i = threadIdx.x; i < cw + hi - lo; i += WG_THREADS) {
                         int idx = start + i;
                         if (idx >= n_az) idx %= n_az;
                         ws[i] = __ldg(srow + idx);
                     }
                 }
                 __syncthreads();
-                for (int i = lane; i < cw; i += 32) {
+                const int i_end = min(cw, (hg + 1) * PER_G);
+                for (int i = hg * PER_G + lane; i < i_end; i += 32) {
                     const float2 gv = gs[i];
 #pragma unroll
-                    for (int t = 0; t < DG_WT; ++t) {
+                    for (int t = 0; t < WG_WT; ++t) {
                         const float2 sv = staged ? ws[i + rel[t]] : __ldg(srow + pmod(t0 + i + rel[t], n_az));
                         acc[t].x = fmaf(gv.x, sv.x, acc[t].x);       // g * conj(s)
                         acc[t].x = fmaf(gv.y, sv.y, acc[t].x);
@@ -150,14 +159,22 @@ weight_grad_kernel(const float2 *__restrict__ g, const float2 *__restrict__ S_t,
             }
         }
 #pragma unroll
-        for (int t = 0; t < DG_WT; ++t) {
+        for (int t = 0; t < WG_WT; ++t) {
 #pragma unroll
             for (int sft = 16; sft > 0; sft >>= 1) {
                 acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, sft);
                 acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, sft);
             }
-            const int k = k0 + warp + t * DG_WARPS;
-            if (lane == 0 && k < K) grad_w[(size_t)r * K + k] = acc[t];
+            if (lane == 0) part[hg][tg + WG_TAPG * t] = acc[t];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < WG_SWEEP; j += WG_THREADS) {
+            const int k = k0 + j;
+            if (k < K) {
+                float2 sum = part[0][j];
+                for (int q = 1; q < WG_THG; ++q) sum = cadd(sum, part[q][j]);
+                grad_w[(size_t)r * K + k] = sum;
+            }
         }
     }
 }
@@ -182,7 +199,7 @@ rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *
 
 rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
                                         int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s) {
-    weight_grad_kernel<<<n_rng, DG_THREADS, 0, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, n_az, K, grad_w);
+    weight_grad_kernel<<<n_rng, WG_THREADS, 0, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, n_az, K, grad_w);
     return check_launch("azimuth_weight_grad");
 }
 

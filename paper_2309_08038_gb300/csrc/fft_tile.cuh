@@ -159,14 +159,6 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
     const int p = threadIdx.x / T;
     const int n = n0 + p;
 
-    if (build_tab) {
-        for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
-            float s, c;
-            sincospif((float)q / (float)L, &s, &c);
-            tab[q] = make_float2(c, -s);
-        }
-    }
-
     float2 v[RM];
     {
         const bool live = n < n_az;
@@ -177,6 +169,15 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
             const float2 x = live ? __ldg(src + m) : make_float2(0.f, 0.f);
             const float wm = win ? __ldg(win + m) : 1.f;
             v[r] = cscale(x, wm);
+        }
+    }
+    // the twiddle table is built while the loads are in flight; the first pass needs no twiddles and
+    // its barrier orders these writes before any read
+    if (build_tab) {
+        for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
+            float s, c;
+            sincospif((float)q / (float)L, &s, &c);
+            tab[q] = make_float2(c, -s);
         }
     }
     float2 *pb = buf + p * PL::LP;
@@ -190,6 +191,9 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
         if constexpr (RR > 1) stockham_pass<L, P, RR, (L / RR), false, true>(v, t, p, pb, buf, tab, centred);
     }
 
+    // the transform is done: a kernel that depends on S (launched for programmatic overlap) may start
+    // its own prologue now; it waits for this grid's completion before reading S.
+    griddep_launch_dependents();
     // coalesced store of the transposed tile: row l holds pulses n0..n0+P-1
     const int np = min(P, n_az - n0);
     if (vec_store && np == P) {

@@ -224,8 +224,10 @@ rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar
     st = launch_range_compress(reinterpret_cast<const float2 *>(raw), win, n_az, L, 1,
                                reinterpret_cast<float2 *>(workspace), s);
     if (st != ROSAR_OK) return st;
+    // the azimuth kernel may overlap the range kernel's tail: before its grid-dependency wait it reads only
+    // H and its own shared memory, and H is not written by the range kernel
     return launch_azimuth_fft(reinterpret_cast<const float2 *>(workspace), reinterpret_cast<const float2 *>(H), L,
-                              n_az, reinterpret_cast<float2 *>(out), s);
+                              n_az, reinterpret_cast<float2 *>(out), s, true);
 }
 
 // ------------------------------------------------------------ differentiable form --

@@ -41,6 +41,13 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may start
+// before its predecessor in the stream has finished; griddep_wait() blocks until that predecessor has
+// completed and its memory is visible, griddep_launch_dependents() lets the successor start early.
+// Both are no-ops when no such launch relation exists.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Non-negative modulo for any int32 value and n >= 1.
 __device__ __forceinline__ int pmod(int a, int n) {
     int r = a % n;
@@ -73,7 +80,10 @@ rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, in
 
 // Azimuth filter in the frequency domain (azimuth_fft.cu).
 int azimuth_fft_supported(int n_az);
-rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s);
+// overlap_predecessor: launch with programmatic stream serialization (only when the preceding kernel in
+// the stream writes S and nothing else the kernel reads before its grid-dependency wait, i.e. H).
+rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
+                                bool overlap_predecessor = false);
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
                                  float2 *H, cudaStream_t s);
 
