@@ -69,13 +69,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world, device):
+    """Largest x over the ranks (the job's time is its slowest rank's).  The reduction tensor lives on
+    the GPU for NCCL and on the host for gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def scan_rotation(b, rank):
+    """Start-angle rotation (in pulses) of rotating buffer b on this rank: every rank images its own scans."""
+    return 211 * b + 17 * rank
 
 
 def measured_peaks():
@@ -170,7 +178,7 @@ def indoor_inputs(torch, device, rank):
     raws = []
     for b in range(N_BUF):
         # distinct scans: the same scene seen from a rotated start angle (a circular shift of the pulses)
-        raws.append(torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, 211 * b + 17 * rank, axis=0))).to(device))
+        raws.append(torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, scan_rotation(b, rank), axis=0))).to(device))
     return cfg, sc, raws, torch.from_numpy(w).to(device), torch.from_numpy(o).to(device), \
         torch.from_numpy(win).to(device)
 

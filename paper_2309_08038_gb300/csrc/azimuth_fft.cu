@@ -36,7 +36,7 @@ struct Layout {
 };
 
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
 azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, RowPlan pl, Layout lay,
                    float2 *__restrict__ out) {
     extern __shared__ float2 sm[];
@@ -46,38 +46,38 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
     const size_t row = (size_t)blockIdx.x * N;
     // prologue independent of S: the H row and the twiddle table
     if (lay.stage_h)
-        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + pad16(n), H + row + n);
+        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + rpad(n, pl.pad_shift), H + row + n);
     cp_async_commit();
     const float2 *tc, *tf;
     build_twiddles(N, lay.full_tab != 0, tw, &tc, &tf);
     griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
-    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + pad16(n), S + row + n);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + rpad(n, pl.pad_shift), S + row + n);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
     row_dif(x, N, pl, tc, tf);
     if (lay.stage_h) {
         for (int n = threadIdx.x; n < N; n += blockDim.x) {   // spectrum times H (same digit-reversed order, carries 1/N), conjugated
-            const float2 y = cmul(hb[pad16(n)], x[pad16(n)]);
-            x[pad16(n)] = make_float2(y.x, -y.y);
+            const float2 y = cmul(hb[rpad(n, pl.pad_shift)], x[rpad(n, pl.pad_shift)]);
+            x[rpad(n, pl.pad_shift)] = make_float2(y.x, -y.y);
         }
     } else {
 #pragma unroll 4
         for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            const float2 y = cmul(__ldg(H + row + n), x[pad16(n)]);
-            x[pad16(n)] = make_float2(y.x, -y.y);
+            const float2 y = cmul(__ldg(H + row + n), x[rpad(n, pl.pad_shift)]);
+            x[rpad(n, pl.pad_shift)] = make_float2(y.x, -y.y);
         }
     }
     __syncthreads();
     row_dit(x, N, pl, tc, tf);
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const float2 y = x[pad16(n)];
+        const float2 y = x[rpad(n, pl.pad_shift)];
         out[row + n] = make_float2(y.x, -y.y);
     }
 }
 
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
 azimuth_plan_kernel(const float2 *__restrict__ w, const int32_t *__restrict__ o, int o_row_stride, int K, int N,
                     RowPlan pl, Layout lay, float2 *__restrict__ H) {
     extern __shared__ float2 sm[];
@@ -92,13 +92,13 @@ azimuth_plan_kernel(const float2 *__restrict__ w, const int32_t *__restrict__ o,
         const long long on = -(long long)__ldg(o + (size_t)r * o_row_stride + k);
         const int n = (int)(((on % N) + N) % N);
         const float2 wv = __ldg(w + (size_t)r * K + k);
-        atomicAdd(&x[pad16(n)].x, wv.x);
-        atomicAdd(&x[pad16(n)].y, wv.y);
+        atomicAdd(&x[rpad(n, pl.pad_shift)].x, wv.x);
+        atomicAdd(&x[rpad(n, pl.pad_shift)].y, wv.y);
     }
     __syncthreads();
     row_dif(x, N, pl, tc, tf);
     const float inv_n = (float)(1.0 / (double)N);
-    for (int n = threadIdx.x; n < N; n += blockDim.x) H[(size_t)r * N + n] = cscale(x[pad16(n)], inv_n);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) H[(size_t)r * N + n] = cscale(x[rpad(n, pl.pad_shift)], inv_n);
 }
 
 constexpr size_t AF_SMEM_CAP = 200 * 1024;
@@ -113,15 +113,16 @@ Layout layout_for(int N, bool with_h) {
     return l;
 }
 
-template <typename F256, typename F512, typename F1024>
-rosar_status launch_rows(int N, int rows, size_t sm, F256 f256, F512 f512, F1024 f1024, const void *k256,
-                         const void *k512, const void *k1024, int (*done)[kMaxDevices], const char *what) {
+template <typename F256, typename F384, typename F512, typename F1024>
+rosar_status launch_rows(int N, int rows, size_t sm, F256 f256, F384 f384, F512 f512, F1024 f1024,
+                         const void *const k[4], int (*done)[kMaxDevices], const char *what) {
     const int T = threads_for(N);
-    const void *k = T <= 256 ? k256 : T <= 512 ? k512 : k1024;
-    rosar_status st = ensure_smem(k, sm, done[T <= 256 ? 0 : T <= 512 ? 1 : 2], what);
+    const int v = T <= 256 ? 0 : T <= 384 ? 1 : T <= 512 ? 2 : 3;
+    rosar_status st = ensure_smem(k[v], sm, done[v], what);
     if (st != ROSAR_OK) return st;
-    if (T <= 256) f256(rows, T, sm);
-    else if (T <= 512) f512(rows, T, sm);
+    if (v == 0) f256(rows, T, sm);
+    else if (v == 1) f384(rows, T, sm);
+    else if (v == 2) f512(rows, T, sm);
     else f1024(rows, T, sm);
     return check_launch(what);
 }
@@ -154,17 +155,19 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
-    static int done[3][kMaxDevices] = {};
+    static int done[4][kMaxDevices] = {};
     const Layout lay = layout_for(n_az, true);
     const bool ov = overlap_predecessor;
     cudaError_t le = cudaSuccess;
+    static const void *const ks[4] = {(const void *)azimuth_fft_kernel<256>, (const void *)azimuth_fft_kernel<384>,
+                                      (const void *)azimuth_fft_kernel<512>, (const void *)azimuth_fft_kernel<1024>};
     rosar_status st = launch_rows(
         n_az, n_rng, lay.bytes,
         [&](int g, int t, size_t sm) { le = launch_fft_rows<256>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<384>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
         [&](int g, int t, size_t sm) { le = launch_fft_rows<512>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
         [&](int g, int t, size_t sm) { le = launch_fft_rows<1024>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
-        (const void *)azimuth_fft_kernel<256>, (const void *)azimuth_fft_kernel<512>,
-        (const void *)azimuth_fft_kernel<1024>, done, "azimuth_fft");
+        ks, done, "azimuth_fft");
     if (st == ROSAR_OK && le != cudaSuccess)
         return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(le));
     return st;
@@ -175,15 +178,17 @@ rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_st
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_plan: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
-    static int done[3][kMaxDevices] = {};
+    static int done[4][kMaxDevices] = {};
     const Layout lay = layout_for(n_az, false);
+    static const void *const ks[4] = {(const void *)azimuth_plan_kernel<256>, (const void *)azimuth_plan_kernel<384>,
+                                      (const void *)azimuth_plan_kernel<512>, (const void *)azimuth_plan_kernel<1024>};
     return launch_rows(
         n_az, n_rng, lay.bytes,
         [&](int g, int t, size_t sm) { azimuth_plan_kernel<256><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
+        [&](int g, int t, size_t sm) { azimuth_plan_kernel<384><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
         [&](int g, int t, size_t sm) { azimuth_plan_kernel<512><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
         [&](int g, int t, size_t sm) { azimuth_plan_kernel<1024><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
-        (const void *)azimuth_plan_kernel<256>, (const void *)azimuth_plan_kernel<512>,
-        (const void *)azimuth_plan_kernel<1024>, done, "azimuth_plan");
+        ks, done, "azimuth_plan");
 }
 
 }  // namespace rosar

@@ -86,19 +86,19 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int n = n0 + u * BT_THREADS;
-            if (n < N) x[rowfft::pad16(n)] = v[u];
+            if (n < N) x[rowfft::rpad(n, sc.plan.pad_shift)] = v[u];
         }
     }
     __syncthreads();
     rowfft::row_dif(x, N, sc.plan, tc, tf);
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
-        const float2 y = cmul(__ldg(sc.H + row + n), x[rowfft::pad16(n)]);
-        x[rowfft::pad16(n)] = make_float2(y.x, -y.y);
+        const float2 y = cmul(__ldg(sc.H + row + n), x[rowfft::rpad(n, sc.plan.pad_shift)]);
+        x[rowfft::rpad(n, sc.plan.pad_shift)] = make_float2(y.x, -y.y);
     }
     __syncthreads();
     rowfft::row_dit(x, N, sc.plan, tc, tf);
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
-        const float2 y = x[rowfft::pad16(n)];
+        const float2 y = x[rowfft::rpad(n, sc.plan.pad_shift)];
         sc.out[row + n] = make_float2(y.x, -y.y);
     }
     __syncthreads();

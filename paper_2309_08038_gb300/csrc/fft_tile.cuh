@@ -70,6 +70,34 @@ __device__ __forceinline__ void dft_dif(float2 *v) {
 
 __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
+// exp(-j*pi*q/L) for 0 <= q < 2L from a two-level table: tab[b] = exp(-j*pi*b/L) for b < 32 and
+// tab[32 + a] = exp(-j*pi*32a/L); a product of two rounded factors (about 1.5 ulp).
+__device__ __forceinline__ float2 half_twiddle(const float2 *tab, int q) {
+    const float2 a = tab[32 + (q >> 5)], b = tab[q & 31];
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+template <int L>
+__device__ __forceinline__ void build_half_twiddles(float2 *tab, int nthreads) {
+    for (int i = threadIdx.x; i < 32 + (2 * L + 31) / 32; i += nthreads) {
+        const int q = i < 32 ? i : 32 * (i - 32);
+        float s, c;
+        sincospif((float)q / (float)L, &s, &c);
+        tab[i] = make_float2(c, -s);
+    }
+}
+
+// wq[q] = w1^q for q = 0..R-1 by squaring and products (depth <= 4 multiplications: a few ulp of error).
+// One table load per butterfly (w1, at a unit stride across threads) replaces R-1 strided loads that
+// would pile onto few shared-memory banks.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w1, float2 (&wq)[R]) {
+    wq[0] = make_float2(1.f, 0.f);
+    if (R > 1) wq[1] = w1;
+#pragma unroll
+    for (int q = 2; q < R; ++q) wq[q] = (q & 1) ? cmul(wq[q - 1], w1) : cmul(wq[q / 2], wq[q / 2]);
+}
+
 // Geometry of a tile of P pulses of length L transformed by T*P threads.
 template <int L, int P_>
 struct Tile {
@@ -83,7 +111,8 @@ struct Tile {
     static constexpr int TP = P + 2;                   // row stride of the transposed tile (16-B aligned)
     static constexpr int BUF = (P * LP > L * TP) ? P * LP : L * TP;
     static constexpr int THREADS = T * P;
-    static constexpr int SMEM_ELEMS = 2 * L + BUF;     // float2 elements: twiddle table + buffer
+    static constexpr int TAB = 32 + ((2 * L + 31) / 32 + 1) / 2 * 2;   // two-level table, even (16-B alignment)
+    static constexpr int SMEM_ELEMS = TAB + BUF;       // float2 elements: twiddle table + buffer
     static constexpr size_t SMEM = sizeof(float2) * (size_t)SMEM_ELEMS;
     static_assert(P % 2 == 0, "pulse tiles hold an even number of pulses");
 };
@@ -108,8 +137,10 @@ __device__ __forceinline__ void stockham_pass(float2 (&v)[Tile<L, P>::RM], int t
         const int j = t + b * T;
         const int k = j & (NS - 1);
         if (NS > 1) {
+            float2 wq[R];
+            twiddle_powers<R>(half_twiddle(tab, 2 * k * (L / (NS * R))), wq);   // W_{NS*R}^(r*k) = (W_{NS*R}^k)^r
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tab[2 * r * k * (L / (NS * R))]);
+            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], wq[r]);
         }
         dft_dif<R>(v + b * R);
     }
@@ -125,15 +156,19 @@ __device__ __forceinline__ void stockham_pass(float2 (&v)[Tile<L, P>::RM], int t
         }
     } else {
         // last pass: NS*R == L, so j < NS and bin l = j + r*NS
+        // centring c_l = (-1)^l exp(-j*pi*l/L) with exp(-j*pi*(j + r*NS)/L) = exp(-j*pi*j/L) * exp(-j*pi*NS/L)^r
+        float2 sp[R];
+        if (centred) twiddle_powers<R>(half_twiddle(tab, NS), sp);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int j = t + b * T;
+            const float2 cj = centred ? half_twiddle(tab, j) : make_float2(1.f, 0.f);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int l = j + r * NS;
                 float2 y = v[b * R + brev(r, ilog2(R))];
                 if (centred) {
-                    const float2 c = tab[l];                      // exp(-j*pi*l/L)
+                    const float2 c = r == 0 ? cj : cmul(cj, sp[r]);
                     y = cmul(y, (l & 1) ? make_float2(-c.x, -c.y) : c);
                 }
                 tile[l * PL::TP + p] = y;
@@ -153,8 +188,8 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
                                            bool vec_store) {
     using PL = Tile<L, P>;
     constexpr int RM = PL::RM, T = PL::T;
-    float2 *tab = smem;               // [2L] exp(-j*pi*q/L)
-    float2 *buf = smem + 2 * L;       // FFT buffer [P][LP], then transposed tile [L][TP]
+    float2 *tab = smem;               // two-level table of exp(-j*pi*q/L), q < 2L
+    float2 *buf = smem + PL::TAB;     // FFT buffer [P][LP], then transposed tile [L][TP]
     const int t = threadIdx.x % T;
     const int p = threadIdx.x / T;
     const int n = n0 + p;
@@ -173,13 +208,7 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
     }
     // the twiddle table is built while the loads are in flight; the first pass needs no twiddles and
     // its barrier orders these writes before any read
-    if (build_tab) {
-        for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
-            float s, c;
-            sincospif((float)q / (float)L, &s, &c);
-            tab[q] = make_float2(c, -s);
-        }
-    }
+    if (build_tab) build_half_twiddles<L>(tab, PL::THREADS);
     float2 *pb = buf + p * PL::LP;
     constexpr int NF = PL::NF, RR = PL::RR;
     if constexpr (L < 16) {
@@ -223,21 +252,17 @@ __device__ __forceinline__ void range_adjoint_tile(const float2 *__restrict__ g,
     using PL = Tile<L, P>;
     constexpr int RM = PL::RM, T = PL::T;
     float2 *tab = smem;
-    float2 *buf = smem + 2 * L;
+    float2 *buf = smem + PL::TAB;
     const int t = threadIdx.x % T;
     const int p = threadIdx.x / T;
     const int np = min(P, n_az - n0);
-    for (int q = threadIdx.x; q < 2 * L; q += PL::THREADS) {
-        float s, c;
-        sincospif((float)q / (float)L, &s, &c);
-        tab[q] = make_float2(c, -s);
-    }
+    build_half_twiddles<L>(tab, PL::THREADS);
     __syncthreads();
     for (int idx = threadIdx.x; idx < L * P; idx += PL::THREADS) {
         const int l = idx / P, q = idx % P;
         float2 x = q < np ? cconj(__ldg(g + (size_t)l * n_az + n0 + q)) : make_float2(0.f, 0.f);
         if (centred) {
-            const float2 c = tab[l];
+            const float2 c = half_twiddle(tab, l);
             x = cmul(x, (l & 1) ? make_float2(-c.x, -c.y) : c);
         }
         buf[q * PL::LP + pad16(l)] = x;

@@ -9,8 +9,9 @@
 // memory.  The window is applied as samples are loaded from HBM; the centring
 // phase c_l is applied in the last pass, which writes the tile transposed
 // ([l][p]) so that the store to the range-major S[l][n0..n0+P) is coalesced
-// along azimuth.  Twiddles come from a per-CTA shared table exp(-j*pi*q/L),
-// q < 2L, built with sincospif.  (fft_tile.cuh holds the tile itself.)
+// along azimuth.  Twiddles come from a two-level per-CTA table of exp(-j*pi*q/L)
+// (32 + 2L/32 entries, built with sincospif), one lookup per butterfly raised to
+// powers.  (fft_tile.cuh holds the tile itself.)
 //
 // Memory-bound: 16 algorithmic bytes per sample (8 read, 8 written).
 

@@ -19,10 +19,15 @@ constexpr int AF_MAXPASS = 16;
 
 struct RowPlan {
     int npass;
+    int pad_shift;            // shared-memory padding: one element per 2^pad_shift (31 = none)
     int rad[AF_MAXPASS];
 };
 
-__host__ __device__ constexpr int padded_len(int n) { return n + n / 16 + 1; }
+// Padding: one element per 16 for power-of-two rows (whose late passes have power-of-two strides), none
+// for rows with an odd factor: their plan puts the power-of-two radix first, where accesses are
+// contiguous, and padding would scramble the odd strides of the later passes.
+__host__ __device__ constexpr int pad_shift_for(int n) { return (n & (n - 1)) == 0 ? 4 : 31; }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> pad_shift_for(n)) + 1; }
 __host__ __device__ constexpr int coarse_len(int n) { return n / 64 + 1; }
 
 // Forward DFT of size R on v[0..R), natural-order output.
@@ -92,7 +97,11 @@ __device__ __forceinline__ void small_dft<8>(float2 *v) { pow2_dft<8>(v); }
 template <>
 __device__ __forceinline__ void small_dft<16>(float2 *v) { pow2_dft<16>(v); }
 
-__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+__device__ __forceinline__ int rpad(int e, int sh) { return e + (e >> sh); }
+
+// Compile-time padding for the passes: PAD = one element per 16, else none.
+template <bool PAD>
+__device__ __forceinline__ int cpad(int e) { return PAD ? e + (e >> 4) : e; }
 
 // floor(i / s) for 0 <= i < 2^23 and 1 <= s <= 2^14, from inv_s = 1/s rounded to float: (i + 1/2)/s is at
 // least 1/(2s) away from an integer while the float product errs by at most about i * 2^-23 / s.
@@ -112,20 +121,11 @@ __device__ __forceinline__ float2 twiddle(int q, const float2 *tc, const float2 
     return tc ? cmul(tc[q >> 6], tf[q & 63]) : tf[q];
 }
 
-// wq[q] = w1^q for q = 1..R-1 by repeated squaring and products (depth <= 4 multiplications, so the
-// rounding error stays within a few ulp).  One table load per butterfly (w1 = W^(j*tstep), consecutive
-// across threads, hence conflict-free) replaces R-1 scattered loads.
-template <int R>
-__device__ __forceinline__ void twiddle_powers(float2 w1, float2 (&wq)[R]) {
-    wq[0] = make_float2(1.f, 0.f);
-    if (R > 1) wq[1] = w1;
-#pragma unroll
-    for (int q = 2; q < R; ++q) wq[q] = (q & 1) ? cmul(wq[q - 1], w1) : cmul(wq[q / 2], wq[q / 2]);
-}
+using fft::twiddle_powers;
 
 // One in-place decimation-in-frequency stage: radix R on blocks of length M (stride s = M/R):
 // v = DFT_R(x[base + r*s]); x[base + q*s] = v[q] * W_M^(j*q).
-template <int R>
+template <int R, bool PAD>
 __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     const int s = M / R, tstep = N / M, nb = N / R;
     const float inv_s = 1.f / (float)s;
@@ -134,19 +134,19 @@ __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *
         const int base = blk * M + j;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x[pad16(base + r * s)];
+        for (int r = 0; r < R; ++r) v[r] = x[cpad<PAD>(base + r * s)];
         small_dft<R>(v);
-        x[pad16(base)] = v[0];
+        x[cpad<PAD>(base)] = v[0];
         float2 wq[R];
         twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
 #pragma unroll
-        for (int q = 1; q < R; ++q) x[pad16(base + q * s)] = cmul(v[q], wq[q]);
+        for (int q = 1; q < R; ++q) x[cpad<PAD>(base + q * s)] = cmul(v[q], wq[q]);
     }
     __syncthreads();
 }
 
 // The transposed stage (decimation in time): v[q] = x[base + q*s] * W_M^(j*q); x[base + r*s] = DFT_R(v)[r].
-template <int R>
+template <int R, bool PAD>
 __device__ __forceinline__ void dit_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     const int s = M / R, tstep = N / M, nb = N / R;
     const float inv_s = 1.f / (float)s;
@@ -156,20 +156,20 @@ __device__ __forceinline__ void dit_pass(float2 *x, int N, int M, const float2 *
         float2 v[R];
         float2 wq[R];
         twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
-        v[0] = x[pad16(base)];
+        v[0] = x[cpad<PAD>(base)];
 #pragma unroll
-        for (int q = 1; q < R; ++q) v[q] = cmul(x[pad16(base + q * s)], wq[q]);
+        for (int q = 1; q < R; ++q) v[q] = cmul(x[cpad<PAD>(base + q * s)], wq[q]);
         small_dft<R>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[pad16(base + r * s)] = v[r];
+        for (int r = 0; r < R; ++r) x[cpad<PAD>(base + r * s)] = v[r];
     }
     __syncthreads();
 }
 
 #define ROSAR_STAGE_CASE(RR) \
-    case RR: DIF ? dif_pass<RR>(x, N, M, tc, tf) : dit_pass<RR>(x, N, M, tc, tf); break;
+    case RR: DIF ? dif_pass<RR, PAD>(x, N, M, tc, tf) : dit_pass<RR, PAD>(x, N, M, tc, tf); break;
 
-template <bool DIF>
+template <bool DIF, bool PAD>
 __device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     switch (R) {
         ROSAR_STAGE_CASE(16)
@@ -177,27 +177,39 @@ __device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const floa
         ROSAR_STAGE_CASE(5)
         ROSAR_STAGE_CASE(4)
         ROSAR_STAGE_CASE(3)
-        default: DIF ? dif_pass<2>(x, N, M, tc, tf) : dit_pass<2>(x, N, M, tc, tf); break;
+        default: DIF ? dif_pass<2, PAD>(x, N, M, tc, tf) : dit_pass<2, PAD>(x, N, M, tc, tf); break;
     }
 }
 #undef ROSAR_STAGE_CASE
 
 // Forward DFT of the row, output in digit-reversed order.
-__device__ __forceinline__ void row_dif(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+template <bool PAD>
+__device__ __forceinline__ void row_dif_t(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
     int M = N;
     for (int p = 0; p < pl.npass; ++p) {
-        stage<true>(pl.rad[p], x, N, M, tc, tf);
+        stage<true, PAD>(pl.rad[p], x, N, M, tc, tf);
         M /= pl.rad[p];
     }
 }
 
+__device__ __forceinline__ void row_dif(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+    if (pl.pad_shift == 4) row_dif_t<true>(x, N, pl, tc, tf);
+    else row_dif_t<false>(x, N, pl, tc, tf);
+}
+
 // Forward DFT of a row held in digit-reversed order, output in natural order.
-__device__ __forceinline__ void row_dit(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+template <bool PAD>
+__device__ __forceinline__ void row_dit_t(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
     int M = 1;
     for (int p = pl.npass - 1; p >= 0; --p) {
         M *= pl.rad[p];
-        stage<false>(pl.rad[p], x, N, M, tc, tf);
+        stage<false, PAD>(pl.rad[p], x, N, M, tc, tf);
     }
+}
+
+__device__ __forceinline__ void row_dit(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
+    if (pl.pad_shift == 4) row_dit_t<true>(x, N, pl, tc, tf);
+    else row_dit_t<false>(x, N, pl, tc, tf);
 }
 
 // Full table (tc == nullptr on return): tw[q] = exp(-2*pi*i*q/N), q < N.  Two-level: tw[0..64) fine, then coarse.
@@ -270,6 +282,7 @@ inline bool make_plan(int N, RowPlan *pl) {
         best[m] = {b, br};
     }
     RowPlan p{};
+    p.pad_shift = pad_shift_for(N);
     int m = N, np = 0;
     bool ok = best[N].second != 0;
     while (ok && m > 1 && np < AF_MAXPASS) {
