@@ -413,6 +413,10 @@ def run_ours(args):
     t_k2f = timed(lambda i: rosar.sparse_azimuth_fft(S_bufs[i % N_BUF], H, out=outs[i % N_BUF])) if fft_ok else None
     t_gather_img = timed(lambda i: rosar.image(raws[i % N_BUF], win, w, o, workspace=S_bufs[i % N_BUF],
                                                 out=outs[i % N_BUF]))
+    import synth as _synth
+    dl = torch.from_numpy(_synth.migration_offsets(cfg, o.cpu().numpy())).to(device)
+    t_mig_img = timed(lambda i: rosar.image_migrating(raws[i % N_BUF], win, w, o, dl, workspace=S_bufs[i % N_BUF],
+                                                      out=outs[i % N_BUF]))
 
     K = cfg.K
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
@@ -456,6 +460,7 @@ def run_ours(args):
                                  f"(sm_max_mhz of {peak_src} peaks)",
                     "algorithmic_flops": k2_flops, "us_per_launch": t_k2 * 1e6}
     paths = {"image_fft_px_s": value if fft_ok else None, "image_gather_px_s": world * px / t_gather_img,
+             "image_migrating_px_s": world * px / t_mig_img,
              "timed_path": "rosar_image_fft" if fft_ok else "rosar_image", "autotune": choice}
 
     # end to end through the public API with pinned host buffers

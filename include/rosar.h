@@ -141,6 +141,24 @@ ROSAR_API rosar_status rosar_image(const rosar_c32 *raw, const float *win, const
                          const int32_t *o, int o_row_stride, int n_az, int L, int K,
                          rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
+/*
+ * Range-migration-aware sparse azimuth filter: Eq. (43) with each tap reading the pulse's
+ * own peak bin (Sec. III-D: the paper picks l*_n of Eq. (40) per pulse), here as a row offset
+ * per (row, tap) computed from the weight design's geometry:
+ *   out[r][theta] = sum_k w[r][k] * S[r + dl[r][k]][(theta + o_k) mod n_az],
+ * rows outside 0 .. n_bins-1 reading zero.  dl = 0 everywhere is rosar_sparse_azimuth.
+ *   S   [n_bins][n_az] complex (in); w [n_rng][K] (in); o as rosar_sparse_azimuth (in);
+ *   dl  [n_rng][K] int32 row offsets, any value (in); out [n_rng][n_az] (out)
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth_migrating(const rosar_c32 *S, int n_bins, const rosar_c32 *w,
+                                                      const int32_t *o, int o_row_stride, const int32_t *dl,
+                                                      int n_rng, int n_az, int K, rosar_c32 *out, void *stream);
+
+/* rosar_image with range-migration-aware taps (rows of S: n_bins = n_rng = L). */
+ROSAR_API rosar_status rosar_image_migrating(const rosar_c32 *raw, const float *win, const rosar_c32 *w,
+                                             const int32_t *o, int o_row_stride, const int32_t *dl, int n_az, int L,
+                                             int K, rosar_c32 *workspace, rosar_c32 *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Frequency-domain form of the sparse azimuth filter.  Eq. (43) with a fixed
  * row is a circular convolution of S[r][.] with g_r, g_r[(-o_k) mod n_az] += w[r][k];

@@ -40,6 +40,7 @@ __all__ = [
     "taylor_taper", "default_weights", "sparse_azimuth_adjoint_S",
     "sparse_azimuth_adjoint_w", "phase_error_grad", "range_compress_adjoint",
     "apply_phase_errors", "image_entropy", "pisr", "half_mainlobe_width",
+    "sparse_azimuth_migrating", "migration_offsets",
 ]
 
 
@@ -216,6 +217,38 @@ def sparse_azimuth(S, w, o):
         for k in range(w.shape[1]):
             out[r] += w[r, k] * S[r, (theta + o[r, k]) % n_az]
     return out
+
+
+def sparse_azimuth_migrating(S, w, o, dl):
+    """Eq. (43) with each tap reading the pulse's own peak bin (Sec. III-D; l*_n of Eq. (40)):
+    out[r, theta] = sum_k w[r, k] * S[r + dl[r, k], (theta + o_k) mod n_az], rows outside
+    0 .. n_bins-1 reading zero.  S: [n_bins, n_az]; w, dl: [n_rng, K]; o: [K] or [n_rng, K]."""
+    S = np.asarray(S, dtype=np.complex128)
+    w = np.asarray(w, dtype=np.complex128)
+    n_bins, n_az = S.shape
+    n_rng = w.shape[0]
+    o = _offsets_per_row(o, n_rng)
+    dl = np.asarray(dl, dtype=np.int64)
+    theta = np.arange(n_az)
+    out = np.zeros((n_rng, n_az), dtype=np.complex128)
+    for r in range(n_rng):
+        for k in range(w.shape[1]):
+            row = r + dl[r, k]
+            if 0 <= row < n_bins:
+                out[r] += w[r, k] * S[row, (theta + o[r, k]) % n_az]
+    return out
+
+
+def migration_offsets(radar: Radar, L, n_az, n_rng, o):
+    """dl[r, k] = l*_{r,k} - r: the peak bin of Eq. (40) at the slant range from the tap's phase centre
+    (offset o_k, nominal radius r0) to the pixel of row r (distance r0 + r*dR), minus the row."""
+    o = _offsets_per_row(o, n_rng)
+    dR = range_bin_spacing(radar, L)
+    dl = np.zeros(o.shape, dtype=np.int64)
+    for r in range(n_rng):
+        R_n = slant_range(radar.r0 + r * dR, 0.0, radar.r0, phase_centre_angle(o[r], n_az))
+        dl[r] = peak_range_bin(R_n, radar, L) - r
+    return dl
 
 
 # -------------------------------------------------------- back-projection --

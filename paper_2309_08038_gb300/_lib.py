@@ -52,6 +52,8 @@ _PROTOS = {
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_sparse_azimuth_migrating": (_I, [_P, _I, _P, _P, _I, _P, _I, _I, _I, _P, _P]),
+    "rosar_image_migrating": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_azimuth_fft_supported": (_I, [_I]),
     "rosar_azimuth_plan": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_fft": (_I, [_P, _P, _I, _I, _P, _P]),

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(BT_THREADS, 3)
 batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs, int n_segs, int total,
              int *counters, int spin_limit, int debug_scan) {
     extern __shared__ __align__(16) char sm[];
-    __shared__ int red[2 * az::THREADS / 32];
+    __shared__ int red[4 * az::THREADS / 32];
     __shared__ int s_ticket, s_abort;
     int *head = counters + CNT_HEAD, *err = counters + CNT_ERR, *done = counters + CNT_DONE;
     int tab_L = 0;   // L of the twiddle table left in shared memory by the previous range tile

@@ -325,4 +325,46 @@ rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, 
                                          reinterpret_cast<float2 *>(grad_raw), static_cast<cudaStream_t>(stream));
 }
 
+// ------------------------------------------------------- range-migration-aware taps --
+
+rosar_status rosar_sparse_azimuth_migrating(const rosar_c32 *S, int n_bins, const rosar_c32 *w, const int32_t *o,
+                                            int o_row_stride, const int32_t *dl, int n_rng, int n_az, int K,
+                                            rosar_c32 *out, void *stream) {
+    clear_error();
+    if (!dl) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_migrating: null dl");
+    if (n_bins < 1) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_migrating: n_bins=%d < 1", n_bins);
+    rosar_status st = check_azimuth_args(S, w, o, o_row_stride, n_rng, n_az, K, out);
+    if (st != ROSAR_OK) return st;
+    if ((long long)n_bins * n_az > kMaxElems || (long long)n_rng * K > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth_migrating: array too large");
+    if (misaligned(dl, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_migrating: misaligned dl");
+    const size_t img = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    if (overlaps(out, img, S, sizeof(rosar_c32) * (size_t)n_bins * n_az) ||
+        overlaps(out, img, dl, sizeof(int32_t) * (size_t)n_rng * K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_migrating: out overlaps an input");
+    return launch_sparse_azimuth_migrating(reinterpret_cast<const float2 *>(S), n_bins,
+                                           reinterpret_cast<const float2 *>(w), o, o_row_stride, dl, n_rng, n_az, K,
+                                           reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_image_migrating(const rosar_c32 *raw, const float *win, const rosar_c32 *w, const int32_t *o,
+                                   int o_row_stride, const int32_t *dl, int n_az, int L, int K, rosar_c32 *workspace,
+                                   rosar_c32 *out, void *stream) {
+    clear_error();
+    rosar_status st = check_range_args(raw, win, n_az, L, workspace);
+    if (st != ROSAR_OK) return st;
+    st = check_azimuth_args(workspace, w, o, o_row_stride, L, n_az, K, out);
+    if (st != ROSAR_OK) return st;
+    if (!dl || misaligned(dl, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "image_migrating: null or misaligned dl");
+    const size_t bytes = sizeof(rosar_c32) * (size_t)n_az * L;
+    if (overlaps(raw, bytes, out, bytes)) return set_error(ROSAR_ERR_INVALID_ARG, "image_migrating: raw and out overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = launch_range_compress(reinterpret_cast<const float2 *>(raw), win, n_az, L, 1,
+                               reinterpret_cast<float2 *>(workspace), s);
+    if (st != ROSAR_OK) return st;
+    return launch_sparse_azimuth_migrating(reinterpret_cast<const float2 *>(workspace), L,
+                                           reinterpret_cast<const float2 *>(w), o, o_row_stride, dl, L, n_az, K,
+                                           reinterpret_cast<float2 *>(out), s);
+}
+
 }  // extern "C"

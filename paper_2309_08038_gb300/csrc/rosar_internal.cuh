@@ -63,6 +63,11 @@ rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
                                    int n_rng, int n_az, int K, float2 *out, cudaStream_t s);
 
+// Range-migration-aware taps: tap k of row r reads row r + dl[r][k] of S (n_bins rows).
+rosar_status launch_sparse_azimuth_migrating(const float2 *S, int n_bins, const float2 *w, const int32_t *o,
+                                             int o_row_stride, const int32_t *dl, int n_rng, int n_az, int K,
+                                             float2 *out, cudaStream_t s);
+
 // Stacked scans [n_scans][n_rng][n_az] sharing w and o; adjoint = conjugated weights, negated offsets.
 rosar_status launch_sparse_azimuth_scans(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
                                          int n_scans, int n_rng, int n_az, int K, bool adjoint, float2 *out,

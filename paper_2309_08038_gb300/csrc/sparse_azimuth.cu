@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(az::THREADS)
 sparse_azimuth_kernel(const float2 *__restrict__ S, const float2 *__restrict__ w, const int32_t *__restrict__ o,
                       int o_row_stride, int n_rng, int n_az, int K, float2 *__restrict__ out) {
     extern __shared__ __align__(16) char sm[];
-    __shared__ int red[2 * az::THREADS / 32];
+    __shared__ int red[4 * az::THREADS / 32];
     const size_t scan = (size_t)blockIdx.z * n_rng * n_az;
     az::azimuth_tile<SA_J, false, ADJ>(S + scan, w, o, o_row_stride, n_az, K, out + scan, blockIdx.y,
                                        blockIdx.x * SaGeo::TW, sm, red);
@@ -40,7 +40,33 @@ rosar_status launch_gather(const float2 *S, const float2 *w, const int32_t *o, i
     return check_launch(ADJ ? "sparse_azimuth_adjoint" : "sparse_azimuth");
 }
 
+using MigGeo = az::GeoMig<SA_J>;
+
+__global__ void __launch_bounds__(az::THREADS)
+sparse_azimuth_mig_kernel(const float2 *__restrict__ S, int n_bins, const float2 *__restrict__ w,
+                          const int32_t *__restrict__ o, int o_row_stride, const int32_t *__restrict__ dl, int n_az,
+                          int K, float2 *__restrict__ out) {
+    extern __shared__ __align__(16) char sm[];
+    __shared__ int red[4 * az::THREADS / 32];
+    az::azimuth_tile<SA_J, false, false, true>(S, w, o, o_row_stride, n_az, K, out, blockIdx.y,
+                                               blockIdx.x * MigGeo::TW, sm, red, dl, n_bins);
+}
+
 }  // namespace
+
+rosar_status launch_sparse_azimuth_migrating(const float2 *S, int n_bins, const float2 *w, const int32_t *o,
+                                             int o_row_stride, const int32_t *dl, int n_rng, int n_az, int K,
+                                             float2 *out, cudaStream_t s) {
+    static int done[kMaxDevices] = {};
+    rosar_status st = ensure_smem((const void *)sparse_azimuth_mig_kernel, MigGeo::SMEM_BYTES, done,
+                                  "sparse_azimuth_migrating");
+    if (st != ROSAR_OK) return st;
+    if (n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth_migrating: n_rng=%d exceeds 65535", n_rng);
+    dim3 grid((n_az + MigGeo::TW - 1) / MigGeo::TW, n_rng);
+    sparse_azimuth_mig_kernel<<<grid, az::THREADS, MigGeo::SMEM_BYTES, s>>>(S, n_bins, w, o, o_row_stride, dl, n_az,
+                                                                           K, out);
+    return check_launch("sparse_azimuth_migrating");
+}
 
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride, int n_rng,
                                    int n_az, int K, float2 *out, cudaStream_t s) {

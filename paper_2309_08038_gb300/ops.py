@@ -264,3 +264,43 @@ def range_compress_adjoint(g, win=None, centred=True, out=None, stream=None):
     check(lib.rosar_range_compress_adjoint(ptr(g), ptr(win), n_az, L, int(bool(centred)), ptr(out),
                                            stream_handle(stream)))
     return out
+
+
+# ------------------------------------------------------------ range-migration-aware taps --
+
+def sparse_azimuth_migrating(S, w, o, dl, n_rng=None, out=None, stream=None):
+    """rosar_sparse_azimuth_migrating: tap k of row r reads row r + dl[r, k] of S [n_bins, n_az]."""
+    lib = _lib.load()
+    require(S, torch.complex64, "S", ndim=2)
+    n_bins, n_az = S.shape
+    require(w, torch.complex64, "w", ndim=2)
+    n_rng = w.shape[0] if n_rng is None else n_rng
+    K = w.shape[1]
+    stride = _offsets(o, n_rng, K)
+    require(dl, torch.int32, "dl", shape=(n_rng, K))
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=S.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_migrating(ptr(S), n_bins, ptr(w), ptr(o), stride, ptr(dl), n_rng, n_az, K,
+                                             ptr(out), stream_handle(stream)))
+    return out
+
+
+def image_migrating(raw, win, w, o, dl, workspace=None, out=None, stream=None):
+    """rosar_image_migrating: range compression, then the migration-aware azimuth filter."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(w, torch.complex64, "w", ndim=2)
+    K = w.shape[1]
+    stride = _offsets(o, L, K)
+    require(dl, torch.int32, "dl", shape=(L, K))
+    if workspace is None:
+        workspace = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    check(lib.rosar_image_migrating(ptr(raw), ptr(win), ptr(w), ptr(o), stride, ptr(dl), n_az, L, K, ptr(workspace),
+                                    ptr(out), stream_handle(stream)))
+    return out

@@ -10,4 +10,4 @@ library nor the oracle.
 from .configs import (CONFIGS, HIGHRES, INDOOR, TINY, RadarParams, ScanConfig,  # noqa: F401
                       batched_configs, diff_configs, max_range)
 from .scene import Scene, draw_offsets, draw_scene, hann_window, make_scene, synth_if  # noqa: F401
-from .weights import default_weights  # noqa: F401
+from .weights import default_weights, migration_offsets  # noqa: F401

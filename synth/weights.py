@@ -46,3 +46,19 @@ def default_weights(cfg: ScanConfig, offsets: np.ndarray, nbar: int = 4, sll_db:
     nrm = np.linalg.norm(v, axis=1, keepdims=True)
     w = np.where(nrm > 0, v / np.where(nrm > 0, nrm, 1.0), 0.0)
     return w.astype(np.complex64)
+
+
+def migration_offsets(cfg: ScanConfig, offsets: np.ndarray) -> np.ndarray:
+    """Row offsets dl[r, k] (int32 [L, K]) of the range-migration-aware filter: tap k of row r reads the
+    bin where a point at that pixel peaks for the tap's phase centre, round(rho/dR) - r (the peak-bin
+    rule of the paper's range FFT), with rho the nominal slant range used by default_weights."""
+    rad = cfg.radar
+    L = cfg.L
+    dR = rad.bin_spacing(L)
+    o = np.asarray(offsets, dtype=np.int64)
+    if o.ndim == 1:
+        o = np.broadcast_to(o, (L, o.shape[0]))
+    R = rad.r0 + np.arange(L, dtype=np.float64)[:, None] * dR
+    dphi = 2.0 * math.pi * o / cfg.n_az
+    rho = np.sqrt(np.maximum(R * R + rad.r0 ** 2 - 2.0 * R * rad.r0 * np.cos(dphi), 0.0))
+    return (np.floor(rho / dR + 0.5) - np.arange(L)[:, None]).astype(np.int32)

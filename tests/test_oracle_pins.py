@@ -336,3 +336,42 @@ def test_pisr_and_mainlobe_hand_cases():
     # right side falls for 3 samples, the left side (wrapping) for 2: the closer minimum wins
     assert O.half_mainlobe_width(np.array([3.0, 2.0, 1.0, 0.5, 0.7, 0.1, 1.5]), 0) == 2
     assert O.half_mainlobe_width(np.array([0.1, 0.5, 2.0, 1.5, 1.0, 0.7, 0.9]), 2) == 2
+
+
+# ------------------------------------------------- range-migration-aware taps --
+
+def test_migrating_filter_reduces_to_fixed_row():
+    rng = np.random.default_rng(9)
+    S = rng.standard_normal((6, 40)) + 1j * rng.standard_normal((6, 40))
+    w = rng.standard_normal((6, 5)) + 1j * rng.standard_normal((6, 5))
+    o = np.array([-7, -2, 0, 3, 9])
+    assert np.array_equal(O.sparse_azimuth_migrating(S, w, o, np.zeros((6, 5), int)), O.sparse_azimuth(S, w, o))
+    # a uniform shift of every tap by one row is the fixed-row filter on the shifted rows (last row reads zero)
+    shifted = O.sparse_azimuth_migrating(S, w, o, np.ones((6, 5), int))
+    np.testing.assert_array_equal(shifted[:5], O.sparse_azimuth(S[1:], w[:5], o))
+    assert not shifted[5].any()
+
+
+def test_migration_offsets_follow_eq40_and_focus_better():
+    """dl[r,k] = l* - r with l* of Eq. (40) at the tap's slant range; reading those bins gathers more of a
+    point target's energy than the fixed row (the paper's Eq. (43) uses l*_n), peak at the same pixel."""
+    L, n_az, M = 256, 3600, 600
+    rad = _radar77(L)
+    dR = O.range_bin_spacing(rad, L)
+    o = np.arange(-M // 2, M // 2, 9)
+    dl = O.migration_offsets(rad, L, n_az, L, o)
+    assert dl[16:].min() == 0 and dl[16:].max() == 1 and dl.max() <= 2   # at +-30 deg: <= 1 bin except near r0
+    r_s, t_s = 4, 1000                                        # a pixel 0.5 m out: the outer taps migrate ~1 bin
+    assert dl[r_s].max() == 1
+    R_t = rad.r0 + r_s * dR
+    raw = O.if_cube(rad, n_az, L, [R_t], [O.phase_centre_angle(t_s, n_az)], [1.0])
+    S = O.range_compress(raw, O.hann_symmetric(L), bins=range(0, r_s + 6))
+    Sw = np.zeros((r_s + 6, n_az), complex)
+    Sw[:] = S
+    rows = slice(r_s - 2, r_s + 3)
+    w = O.default_weights(rad, L, n_az, L, o, M)[rows]
+    fixed = O.sparse_azimuth(Sw[rows], w, o)
+    mig = O.sparse_azimuth_migrating(Sw[r_s - 2:], w, o, dl[rows])
+    assert np.unravel_index(np.argmax(np.abs(fixed)), fixed.shape) == (2, t_s)
+    assert np.unravel_index(np.argmax(np.abs(mig)), mig.shape) == (2, t_s)
+    assert np.abs(mig[2, t_s]) > 1.01 * np.abs(fixed[2, t_s])

@@ -57,3 +57,11 @@ def test_scene_draws_are_reproducible():
 
 def test_hann_window():
     np.testing.assert_allclose(synth.hann_window(64), O.hann_symmetric(64), atol=1e-7)
+
+
+def test_migration_offsets_match_oracle():
+    for cfg in (synth.TINY, synth.INDOOR):
+        o = synth.draw_offsets(cfg)
+        got = synth.migration_offsets(cfg, o)
+        ref = O.migration_offsets(_oracle_radar(cfg), cfg.L, cfg.n_az, cfg.L, o)
+        assert got.dtype == np.int32 and np.array_equal(got, ref)
