@@ -40,7 +40,8 @@ __all__ = [
     "taylor_taper", "default_weights", "sparse_azimuth_adjoint_S",
     "sparse_azimuth_adjoint_w", "phase_error_grad", "range_compress_adjoint",
     "apply_phase_errors", "image_entropy", "pisr", "half_mainlobe_width",
-    "sparse_azimuth_migrating", "migration_offsets",
+    "sparse_azimuth_migrating", "migration_offsets", "bpa_time_pixels", "bpa_time",
+    "sas_time_pixels", "sas_time",
 ]
 
 
@@ -312,6 +313,133 @@ def bpa(S, radar: Radar, n_rng, M_ap, interp="linear", dphi=None, dr=None):
     out = np.zeros((n_rng, n_az), dtype=np.complex128)
     for r in range(n_rng):
         out[r] = bpa_pixels(S, radar, n_az, M_ap, np.full(n_az, r), thetas, interp, dphi, dr)
+    return out
+
+
+# ------------------------------------------------ time-domain BPA and SAS --
+
+def _fast_time_compensation(radar: Radar, rho, win, L, m_ref):
+    """win[m] * exp(-j*2*pi*tau*K*t_s*(m - m_ref)), tau = 2*rho/c, for every slant range in ``rho``.
+
+    This is one column of W_BP (Eq. (14)) or W_SA (Sec. III-A) without its per-pulse factor: the
+    fast-time phase of a return from slant range rho, removed sample by sample.  Returns
+    rho.shape + (L,)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    m = np.arange(L, dtype=np.float64) - m_ref
+    tau = 2.0 * rho / radar.c
+    return win * np.exp(-2j * math.pi * (tau * radar.slope * radar.t_s)[..., None] * m)
+
+
+def _window(win, L):
+    return np.ones(L) if win is None else np.asarray(win, dtype=np.float64)
+
+
+def bpa_time_pixels(raw, win, radar: Radar, n_az, M_ap, rows, thetas):
+    """Time-domain back-projection at selected polar pixels, the paper's "BPA" (Sec. II-C, Eq. (14)).
+
+    I(phi, R) = sum over the M_ap pulses n = (theta + d) mod n_az, d = -M_ap/2 .. M_ap/2-1, and the
+    L fast-time samples m of alpha_n * exp(-j*2*pi*tau_n*K*m*t_s) * exp(-j*2*k*R_n) * win[m] * raw[n, m]:
+    the Hadamard product of W_BP and Y_IF summed over both axes.  R_n by Eq. (2) at the nominal
+    phase-centre position (r0, 2*pi*n/n_az), tau_n = 2*R_n/c, alpha_n = p(theta_n) by Eqs. (3), (8),
+    (15), k = 2*pi*(K*T_Start + fc)/c.  ``win`` = None is Eq. (14) verbatim; a window multiplies the
+    fast-time samples as in the range compression.  raw: [n_az, L] pulse-major.
+    """
+    raw = np.asarray(raw, dtype=np.complex128)
+    L = raw.shape[1]
+    win = _window(win, L)
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1)
+    thetas = np.asarray(thetas, dtype=np.int64).reshape(-1)
+    dR = range_bin_spacing(radar, L)
+    k = wavenumber(radar)
+    d = np.arange(-(M_ap // 2), M_ap - M_ap // 2)
+    out = np.zeros(rows.shape[0], dtype=np.complex128)
+    for p in range(rows.shape[0]):
+        n = (thetas[p] + d) % n_az
+        R = radar.r0 + rows[p] * dR
+        phi = phase_centre_angle(thetas[p], n_az)
+        phi_n = phase_centre_angle(n, n_az)
+        R_n = slant_range(R, phi, radar.r0, phi_n)
+        alpha = np.where(R_n == 0.0, 1.0, antenna_pattern(off_boresight_angle(R, phi, radar.r0, phi_n)))
+        W = (alpha * np.exp(-2j * k * R_n))[:, None] * _fast_time_compensation(radar, R_n, win, L, 0.0)
+        out[p] = np.sum(W * raw[n])
+    return out
+
+
+def bpa_time(raw, win, radar: Radar, n_rng, M_ap):
+    """Full polar time-domain BPA image [n_rng, n_az] (Eq. (14) at every pixel).
+
+    Row by row: with nominal geometry, tap d of every pixel in row r sees the same slant range R_d,
+    so the fast-time sums D[n, d] = sum_m W_BP[m, d] * raw[n, m] are one matrix product and
+    I(r, theta) = sum_d D[(theta + d) mod n_az, d]."""
+    raw = np.asarray(raw, dtype=np.complex128)
+    n_az, L = raw.shape
+    win = _window(win, L)
+    dR = range_bin_spacing(radar, L)
+    k = wavenumber(radar)
+    d = np.arange(-(M_ap // 2), M_ap - M_ap // 2)
+    theta = np.arange(n_az)
+    phi_d = phase_centre_angle(d, n_az)
+    out = np.zeros((n_rng, n_az), dtype=np.complex128)
+    for r in range(n_rng):
+        R = radar.r0 + r * dR
+        R_d = slant_range(R, 0.0, radar.r0, phi_d)
+        alpha = np.where(R_d == 0.0, 1.0, antenna_pattern(off_boresight_angle(R, 0.0, radar.r0, phi_d)))
+        W = (alpha * np.exp(-2j * k * R_d))[:, None] * _fast_time_compensation(radar, R_d, win, L, 0.0)
+        D = raw @ W.T                                                   # [n_az, M_ap]
+        out[r] = np.sum(D[(theta[:, None] + d[None, :]) % n_az, np.arange(M_ap)[None, :]], axis=1)
+    return out
+
+
+def sas_time_pixels(raw, win, w, o, radar: Radar, n_az, rows, thetas, centred=True):
+    """Time-domain sparse-aperture imaging at selected pixels, the paper's "SAS" (Algorithm 2).
+
+    I(r, theta) = sum_k w[r, k] * sum_m W_SA[m, k] * win[m] * raw[(theta + o_k) mod n_az, m], the
+    Khatri-Rao form 1^T (w^H o (W_SA . Y_IF')) 1 of Sec. III-A with the stored weights w = conj of the
+    paper's w (as in Eq. (43) here).  W_SA[m, k] = exp(-j*2*pi*tau_k*K*t_s*(m - m_ref)) with tau_k
+    = 2*rho_k/c and rho_k the nominal slant range from the phase centre at pulse offset o_k to the
+    pixel (Eq. (2)).  m_ref = 0 is W_SA verbatim (it pairs with weights built with k of Sec. II-B);
+    centred=True takes m_ref = (L-1)/2, which pairs with weights built with k_mid.
+    w: [n_rng, K]; o: [K] shared or [n_rng, K] per row.
+    """
+    raw = np.asarray(raw, dtype=np.complex128)
+    L = raw.shape[1]
+    win = _window(win, L)
+    m_ref = (L - 1) / 2.0 if centred else 0.0
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1)
+    thetas = np.asarray(thetas, dtype=np.int64).reshape(-1)
+    w = np.asarray(w, dtype=np.complex128)
+    orow = _offsets_per_row(o, w.shape[0])
+    dR = range_bin_spacing(radar, L)
+    out = np.zeros(rows.shape[0], dtype=np.complex128)
+    for p in range(rows.shape[0]):
+        r = rows[p]
+        ok = orow[r]
+        rho = slant_range(radar.r0 + r * dR, 0.0, radar.r0, phase_centre_angle(ok, n_az))
+        E = _fast_time_compensation(radar, rho, win, L, m_ref)           # [K, L]
+        n = (thetas[p] + ok) % n_az
+        out[p] = np.sum(w[r] * np.sum(E * raw[n], axis=1))
+    return out
+
+
+def sas_time(raw, win, w, o, radar: Radar, n_rng, centred=True):
+    """Full polar time-domain SAS image [n_rng, n_az] (Algorithm 2 at every pixel), row by row:
+    D[n, k] = sum_m W_SA[m, k] * win[m] * raw[n, m] is one matrix product per row, and
+    I(r, theta) = sum_k w[r, k] * D[(theta + o_k) mod n_az, k]."""
+    raw = np.asarray(raw, dtype=np.complex128)
+    n_az, L = raw.shape
+    win = _window(win, L)
+    m_ref = (L - 1) / 2.0 if centred else 0.0
+    w = np.asarray(w, dtype=np.complex128)
+    orow = _offsets_per_row(o, n_rng)
+    dR = range_bin_spacing(radar, L)
+    theta = np.arange(n_az)
+    out = np.zeros((n_rng, n_az), dtype=np.complex128)
+    for r in range(n_rng):
+        ok = orow[r]
+        rho = slant_range(radar.r0 + r * dR, 0.0, radar.r0, phase_centre_angle(ok, n_az))
+        D = raw @ _fast_time_compensation(radar, rho, win, L, m_ref).T   # [n_az, K]
+        out[r] = np.sum(w[r][None, :] * D[(theta[:, None] + ok[None, :]) % n_az, np.arange(ok.shape[0])[None, :]],
+                        axis=1)
     return out
 
 

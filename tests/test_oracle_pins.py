@@ -375,3 +375,141 @@ def test_migration_offsets_follow_eq40_and_focus_better():
     assert np.unravel_index(np.argmax(np.abs(fixed)), fixed.shape) == (2, t_s)
     assert np.unravel_index(np.argmax(np.abs(mig)), mig.shape) == (2, t_s)
     assert np.abs(mig[2, t_s]) > 1.01 * np.abs(fixed[2, t_s])
+
+
+# ------------------------------------------------- time-domain BPA and SAS --
+
+def _rand_raw(rng, n_az, L):
+    return rng.standard_normal((n_az, L)) + 1j * rng.standard_normal((n_az, L))
+
+
+@pytest.mark.parametrize("centred", [False, True])
+def test_time_domain_sas_with_one_facing_tap_is_the_range_dft(centred):
+    """A single tap at pulse offset 0 sees the pixel of row r at slant range exactly r*dR, so W_SA's
+    fast-time compensation is the DFT row of bin r (Eq. (38)/(40)): SAS with o = [0], w = 1 is the
+    range compression, centred or not."""
+    L, n_az = 64, 40
+    rad = _radar77(L)
+    rng = np.random.default_rng(21)
+    raw = _rand_raw(rng, n_az, L)
+    win = O.hann_symmetric(L)
+    got = O.sas_time(raw, win, np.ones((L, 1)), np.array([0]), rad, L, centred=centred)
+    ref = O.range_compress(raw, win, centred=centred)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_time_domain_bpa_with_one_pulse_equals_fft_bpa():
+    """With M_ap = 1 the only tap faces the pixel, its slant range is r*dR, a whole bin: the
+    time-domain BPA of Eq. (14) (k, fast time from m = 0) equals the range-compressed BPA (k_mid,
+    centred DFT, nearest bin) -- the two phase references differ by exactly the centring factor."""
+    L, n_az = 64, 30
+    rad = _radar77(L)
+    rng = np.random.default_rng(22)
+    raw = _rand_raw(rng, n_az, L)
+    win = O.hann_symmetric(L)
+    got = O.bpa_time(raw, win, rad, L, 1)
+    ref = O.bpa(O.range_compress(raw, win), rad, L, 1, interp="nearest")
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("use_win", [False, True])
+def test_time_domain_bpa_compensates_a_point_at_the_pixel_exactly(use_win):
+    """Sec. II-C: for a target at the imaged point every phase of W_BP . Y_IF cancels, so Eq. (14)
+    returns A * sum_n p(theta_n)^2 * sum_m win[m] (amplitude of Eq. (15) times alpha_n = p(theta_n))."""
+    L, n_az, M = 64, 360, 60
+    rad = _radar77(L)
+    dR = O.range_bin_spacing(rad, L)
+    r_t, th_t, A = 25, 123, 0.7 - 0.4j
+    R_t, phi_t = rad.r0 + r_t * dR, O.phase_centre_angle(th_t, n_az)
+    raw = O.if_cube(rad, n_az, L, [R_t], [phi_t], [A])
+    win = O.hann_symmetric(L) if use_win else None
+    d = np.arange(-(M // 2), M - M // 2)
+    phi_n = O.phase_centre_angle(th_t + d, n_az)
+    p = O.antenna_pattern(O.off_boresight_angle(R_t, phi_t, rad.r0, phi_n))
+    expect = A * np.sum(p * p) * (np.sum(win) if use_win else L)
+    got = O.bpa_time_pixels(raw, win, rad, n_az, M, [r_t], [th_t])[0]
+    assert abs(got - expect) <= 1e-9 * abs(expect)
+    img = O.bpa_time(raw, win, rad, L, M)
+    assert abs(img[r_t, th_t] - expect) <= 1e-9 * abs(expect)
+    assert _peak_with_margin(img) == (r_t, th_t)
+
+
+@pytest.mark.parametrize("centred", [False, True])
+def test_time_domain_sas_with_matched_weights_is_fully_compensated(centred):
+    """Algorithm 2 with w = conj(steering vector)/norm (Eq. (16), wavenumber k with W_SA verbatim,
+    k_mid with the centred W_SA) returns A * sum(T p^2)/||T p|| * sum win at the target's own pixel."""
+    L, n_az, K, M = 64, 360, 16, 60
+    rad = _radar77(L)
+    dR = O.range_bin_spacing(rad, L)
+    r_t, th_t, A = 30, 7, 1.3 + 0.2j
+    raw = O.if_cube(rad, n_az, L, [rad.r0 + r_t * dR], [O.phase_centre_angle(th_t, n_az)], [A])
+    win = O.hann_symmetric(L)
+    o = np.sort(np.random.default_rng(100).choice(M, K, replace=False)) - M // 2
+    R = rad.r0 + r_t * dR
+    rho = O.slant_range(R, 0.0, rad.r0, O.phase_centre_angle(o, n_az))
+    p = O.antenna_pattern(O.off_boresight_angle(R, 0.0, rad.r0, O.phase_centre_angle(o, n_az)))
+    T = O.taylor_taper(M)[o + M // 2]
+    kk = O.wavenumber_centred(rad, L) if centred else O.wavenumber(rad)
+    v = T * p * np.exp(-2j * kk * rho)
+    w = np.zeros((L, K), dtype=np.complex128)
+    w[r_t] = v / np.linalg.norm(v)
+    expect = A * np.sum(T * p * p) / np.linalg.norm(T * p) * np.sum(win)
+    got = O.sas_time_pixels(raw, win, w, o, rad, n_az, [r_t], [th_t], centred=centred)[0]
+    assert abs(got - expect) <= 1e-9 * abs(expect)
+    img = O.sas_time(raw, win, w, o, rad, L, centred=centred)
+    assert abs(img[r_t, th_t] - expect) <= 1e-9 * abs(expect)
+
+
+def test_time_domain_forms_match_brute_force_loops():
+    """Scalar loops straight from Eq. (14) and Algorithm 2 (math module, no numpy broadcasting) on a
+    tiny cube; the vectorised full-image and per-pixel forms must agree with them everywhere."""
+    L, n_az, K, M, n_rng = 6, 11, 3, 4, 5
+    rad = O.Radar(fc=77e9, slope=1e14, t_s=4e-6, t_start=8e-6, r0=0.25)
+    rng = np.random.default_rng(23)
+    raw = _rand_raw(rng, n_az, L)
+    win = rng.uniform(0.2, 1.0, L)
+    w = rng.standard_normal((n_rng, K)) + 1j * rng.standard_normal((n_rng, K))
+    o = np.array([-5, 1, 3])
+    dR = rad.c / (2 * rad.slope * rad.t_s * L)
+    k = 2 * math.pi * (rad.slope * rad.t_start + rad.fc) / rad.c
+    bpa = np.zeros((n_rng, n_az), dtype=complex)
+    sas = np.zeros((n_rng, n_az), dtype=complex)
+    for r in range(n_rng):
+        R = rad.r0 + r * dR
+        for t in range(n_az):
+            for d in range(-(M // 2), M - M // 2):
+                n = (t + d) % n_az
+                dphi = 2 * math.pi * (n - t) / n_az
+                Rn = math.sqrt(R * R + rad.r0 ** 2 - 2 * R * rad.r0 * math.cos(dphi))
+                th = math.atan2(R * math.sin(abs(dphi)), R * math.cos(abs(dphi)) - rad.r0)
+                a = math.cos(th) if abs(th) < math.pi / 2 else 0.0
+                tau = 2 * Rn / rad.c
+                for m in range(L):
+                    W = a * complex(math.cos(-2 * math.pi * tau * rad.slope * m * rad.t_s - 2 * k * Rn),
+                                    math.sin(-2 * math.pi * tau * rad.slope * m * rad.t_s - 2 * k * Rn))
+                    bpa[r, t] += W * win[m] * raw[n, m]
+            for kk in range(K):
+                n = (t + o[kk]) % n_az
+                dphi = 2 * math.pi * o[kk] / n_az
+                rho = math.sqrt(R * R + rad.r0 ** 2 - 2 * R * rad.r0 * math.cos(dphi))
+                tau = 2 * rho / rad.c
+                acc = 0j
+                for m in range(L):
+                    ph = -2 * math.pi * tau * rad.slope * rad.t_s * (m - (L - 1) / 2)
+                    acc += complex(math.cos(ph), math.sin(ph)) * win[m] * raw[n, m]
+                sas[r, t] += w[r, kk] * acc
+    tol = 1e-10 * np.abs(bpa).max()
+    np.testing.assert_allclose(O.bpa_time(raw, win, rad, n_rng, M), bpa, rtol=0, atol=tol)
+    rr, tt = np.meshgrid(np.arange(n_rng), np.arange(n_az), indexing="ij")
+    np.testing.assert_allclose(O.bpa_time_pixels(raw, win, rad, n_az, M, rr, tt).reshape(n_rng, n_az), bpa,
+                               rtol=0, atol=tol)
+    tol = 1e-10 * np.abs(sas).max()
+    np.testing.assert_allclose(O.sas_time(raw, win, w, o, rad, n_rng), sas, rtol=0, atol=tol)
+    np.testing.assert_allclose(O.sas_time_pixels(raw, win, w, o, rad, n_az, rr, tt).reshape(n_rng, n_az), sas,
+                               rtol=0, atol=tol)
+    # per-row offsets: row r of a per-row table equal to o everywhere but one row
+    orow = np.tile(o, (n_rng, 1))
+    orow[2] = [-1, 0, 4]
+    img = O.sas_time(raw, win, w, orow, rad, n_rng)
+    np.testing.assert_allclose(np.delete(img, 2, axis=0), np.delete(sas, 2, axis=0), rtol=0, atol=tol)
+    assert np.abs(img[2] - sas[2]).max() > 1e-3 * np.abs(sas).max()
