@@ -160,6 +160,51 @@ ROSAR_API rosar_status rosar_image_migrating(const rosar_c32 *raw, const float *
                                              int K, rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Time-domain comparison paths: the paper's "BPA" (Sec. II-C, Eq. (14)) and
+ * "SAS" (Sec. III-A, Algorithm 2 with W_SA).  Both read the raw IF cube and
+ * sum over taps k and fast-time samples m:
+ *   out[r][theta] = sum_k c[r][k] * sum_m win[m] * exp(-j*2*pi*tau_k*K*t_s*(m - m_ref))
+ *                                   * raw[(theta + o_k) mod n_az][m],
+ * tau_k = 2*rho_k/c with rho_k the nominal slant range (Eq. (2)) from the phase
+ * centre at radius r0 and angle 2*pi*(theta + o_k)/n_az to the pixel at
+ * distance R_r = r0 + r*dR and angle 2*pi*theta/n_az, dR = c/(2*K*t_s*L).
+ * Cost O(K*L) per pixel (the FFT+ forms cost O(K)); FP32 arithmetic with the
+ * per-(r, k) slant range and two-way phase in FP64.  win may be NULL (all
+ * ones, the paper's unwindowed sums).  Requires L a multiple of 16 and raw
+ * 16-byte aligned.  out must not overlap raw.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Time-domain BPA (Eq. (14)): taps o_k = d = -M_ap/2 .. M_ap-M_ap/2-1 (all pulses
+ * of the aperture), c = alpha_d * exp(-j*2*k*rho_d), alpha_d = max(0, cos of the
+ * off-bore-sight angle) (Eqs. (3), (8), (15)), 1 when rho_d = 0; m_ref = 0,
+ * k = 2*pi*(fc + K*T_start)/c.  (Evaluated referenced to the window centre with
+ * k_mid, which is the same product.)  Nominal geometry only.
+ *   raw   [n_az][L] complex, pulse-major                                   (in)
+ *   win   [L] float or NULL                                                (in)
+ *   radar host pointer                                                     (in)
+ *   out   [n_rng][n_az] complex                                           (out)
+ * Limits: n_rng >= 1; 1 <= M_ap <= n_az; 16 <= L <= 65536, L % 16 == 0.
+ */
+ROSAR_API rosar_status rosar_bpa_time(const rosar_c32 *raw, const float *win, const rosar_radar *radar, int n_az,
+                                      int L, int n_rng, int M_ap, rosar_c32 *out, void *stream);
+
+/*
+ * Time-domain SAS (Algorithm 2): taps o_k and coefficients c = w[r][k] from the
+ * caller (layout and offset rules as in rosar_sparse_azimuth: o shared [K] if
+ * o_row_stride == 0, else per row; any int32 value, taken modulo n_az).  m_ref =
+ * (L-1)/2 if centred (pairs with weights built with the wavenumber at the
+ * window centre, as rosar_image's weights are), else 0 (W_SA verbatim, pairs
+ * with weights built with k).
+ *   raw [n_az][L] complex (in); win [L] float or NULL (in); w [n_rng][K] (in);
+ *   out [n_rng][n_az] complex (out).
+ * Limits: n_rng, K >= 1; 16 <= L <= 65536, L % 16 == 0; centred in {0, 1}.
+ */
+ROSAR_API rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, const rosar_c32 *w, const int32_t *o,
+                                      int o_row_stride, const rosar_radar *radar, int n_az, int L, int n_rng, int K,
+                                      int centred, rosar_c32 *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Frequency-domain form of the sparse azimuth filter.  Eq. (43) with a fixed
  * row is a circular convolution of S[r][.] with g_r, g_r[(-o_k) mod n_az] += w[r][k];
  * it equals IFFT(H_r * FFT(S[r][.])) with H_r = FFT(g_r)/n_az.  H depends only on

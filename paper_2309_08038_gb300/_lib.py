@@ -51,6 +51,8 @@ _PROTOS = {
     "rosar_sparse_azimuth": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_bpa_time": (_I, [_P, _P, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _P, _P]),
+    "rosar_sas_time": (_I, [_P, _P, _P, _P, _I, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_migrating": (_I, [_P, _I, _P, _P, _I, _P, _I, _I, _I, _P, _P]),
     "rosar_image_migrating": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),

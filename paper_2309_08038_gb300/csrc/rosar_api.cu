@@ -158,6 +158,74 @@ rosar_status rosar_bpa(const rosar_c32 *S, const rosar_radar *radar, const float
                       reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+
+rosar_status time_domain_params(const char *what, const rosar_c32 *raw, const rosar_radar *radar, int n_az, int L,
+                                int n_rng, int K, bool centred, const rosar_c32 *out, TdParams *p) {
+    if (!raw || !radar || !out) return set_error(ROSAR_ERR_INVALID_ARG, "%s: null raw, radar or out", what);
+    if (n_az < 1 || n_rng < 1 || K < 1 || L < 16 || L > 65536)
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: need n_az, n_rng, K >= 1 and 16 <= L <= 65536 (n_az=%d L=%d "
+                         "n_rng=%d K=%d)", what, n_az, L, n_rng, K);
+    if (L % time_domain_sample_multiple() != 0)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: L=%d is not a multiple of %d", what, L,
+                         time_domain_sample_multiple());
+    if ((long long)n_az * L > kMaxElems || (long long)n_rng * n_az > kMaxElems || (long long)n_rng * K > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: sizes too large", what);
+    if (misaligned(raw, 16) || misaligned(out, 8)) return set_error(ROSAR_ERR_INVALID_ARG, "%s: misaligned pointer", what);
+    const double c = radar->c_mps > 0 ? radar->c_mps : 299792458.0;
+    if (!(radar->slope_hz_per_s > 0) || !(radar->t_sample_s > 0) || !(radar->r0_m >= 0) || !(radar->fc_hz > 0))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: radar parameters must be positive", what);
+    if (overlaps(out, sizeof(rosar_c32) * (size_t)n_rng * n_az, raw, sizeof(rosar_c32) * (size_t)n_az * L))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: out overlaps raw", what);
+    p->dR = c / (2.0 * radar->slope_hz_per_s * radar->t_sample_s * L);
+    const double f_mid = radar->fc_hz + radar->slope_hz_per_s * (radar->t_start_s + radar->t_sample_s * (L - 1) / 2.0);
+    p->two_f_over_c = 2.0 * f_mid / c;
+    p->phi_scale = 2.0 / (p->dR * L);
+    p->r0 = radar->r0_m;
+    p->m_ref = centred ? 0.5f * (float)(L - 1) : 0.f;
+    p->n_az = n_az;
+    p->L = L;
+    p->n_rng = n_rng;
+    return ROSAR_OK;
+}
+
+}  // namespace
+
+rosar_status rosar_bpa_time(const rosar_c32 *raw, const float *win, const rosar_radar *radar, int n_az, int L,
+                            int n_rng, int M_ap, rosar_c32 *out, void *stream) {
+    clear_error();
+    TdParams p;
+    rosar_status st = time_domain_params("bpa_time", raw, radar, n_az, L, n_rng, M_ap, true, out, &p);
+    if (st != ROSAR_OK) return st;
+    if (M_ap > n_az) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time: M_ap=%d exceeds n_az=%d", M_ap, n_az);
+    if (win && misaligned(win, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time: misaligned win");
+    return launch_time_domain(reinterpret_cast<const float2 *>(raw), win, nullptr, nullptr, 0, p, M_ap, true,
+                              reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, const rosar_c32 *w, const int32_t *o,
+                            int o_row_stride, const rosar_radar *radar, int n_az, int L, int n_rng, int K, int centred,
+                            rosar_c32 *out, void *stream) {
+    clear_error();
+    if (centred != 0 && centred != 1) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time: centred must be 0 or 1");
+    TdParams p;
+    rosar_status st = time_domain_params("sas_time", raw, radar, n_az, L, n_rng, K, centred == 1, out, &p);
+    if (st != ROSAR_OK) return st;
+    if (!w || !o) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time: null w or o");
+    if (o_row_stride != 0 && o_row_stride < K)
+        return set_error(ROSAR_ERR_INVALID_ARG, "sas_time: o_row_stride=%d must be 0 or >= K=%d", o_row_stride, K);
+    if ((long long)n_rng * o_row_stride > kMaxElems) return set_error(ROSAR_ERR_UNSUPPORTED, "sas_time: o too large");
+    if (misaligned(w, 8) || misaligned(o, 4) || (win && misaligned(win, 4)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sas_time: misaligned pointer");
+    const size_t img = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    const size_t ob = sizeof(int32_t) * (o_row_stride ? (size_t)(n_rng - 1) * o_row_stride + K : (size_t)K);
+    if (overlaps(out, img, w, sizeof(rosar_c32) * (size_t)n_rng * K) || overlaps(out, img, o, ob))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sas_time: out overlaps w or o");
+    return launch_time_domain(reinterpret_cast<const float2 *>(raw), win, reinterpret_cast<const float2 *>(w), o,
+                              o_row_stride, p, K, false, reinterpret_cast<float2 *>(out),
+                              static_cast<cudaStream_t>(stream));
+}
+
 rosar_status rosar_image(const rosar_c32 *raw, const float *win, const rosar_c32 *w, const int32_t *o,
                          int o_row_stride, int n_az, int L, int K, rosar_c32 *workspace, rosar_c32 *out, void *stream) {
     clear_error();

@@ -100,6 +100,22 @@ struct BpaParams {
     double r0;
 };
 
+// Time-domain BPA / SAS (time_domain.cu).  phi_scale = 2/(dR*L): half-turns of fast-time phase per
+// sample per metre of slant range; two_f_over_c = 2*f_mid/c; m_ref = fast-time phase reference sample.
+struct TdParams {
+    double dR;
+    double r0;
+    double two_f_over_c;
+    double phi_scale;
+    float m_ref;
+    int n_az;
+    int L;
+    int n_rng;
+};
+int time_domain_sample_multiple();
+rosar_status launch_time_domain(const float2 *raw, const float *win, const float2 *w, const int32_t *o,
+                                int o_row_stride, const TdParams &p, int K, bool bpa, float2 *out, cudaStream_t s);
+
 rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, const float *dr, int L, int n_rng,
                         int n_az, int M_ap, int interp, float2 *out, cudaStream_t s);
 

@@ -98,6 +98,42 @@ def bpa(S, radar: Radar, n_rng, M_ap, interp="linear", dphi=None, dr=None, out=N
     return out
 
 
+def bpa_time(raw, win, radar: Radar, n_rng, M_ap, out=None, stream=None):
+    """rosar_bpa_time: time-domain back-projection (Eq. (14)) of the raw cube [n_az, L] onto rows 0..n_rng-1."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    st = radar.as_struct()
+    check(lib.rosar_bpa_time(ptr(raw), ptr(win), ctypes.byref(st), n_az, L, n_rng, M_ap, ptr(out),
+                             stream_handle(stream)))
+    return out
+
+
+def sas_time(raw, win, w, o, radar: Radar, centred=True, out=None, stream=None):
+    """rosar_sas_time: time-domain sparse-aperture imaging (Algorithm 2) of the raw cube [n_az, L]; one output
+    row per row of w [n_rng, K]."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(w, torch.complex64, "w", ndim=2)
+    n_rng, K = w.shape
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    st = radar.as_struct()
+    check(lib.rosar_sas_time(ptr(raw), ptr(win), ptr(w), ptr(o), stride, ctypes.byref(st), n_az, L, n_rng, K,
+                             1 if centred else 0, ptr(out), stream_handle(stream)))
+    return out
+
+
 def image(raw, win, w, o, workspace=None, out=None, stream=None):
     """rosar_image: range compression into `workspace`, then the sparse azimuth filter into `out`."""
     lib = _lib.load()

@@ -81,6 +81,24 @@ def test_bpa_rejects_bad_arguments(lib):
     assert f(FAKE, None, None, None, 64, 64, 360, 60, 1, FAKE2, None) == 1
 
 
+def test_time_domain_rejects_bad_arguments(lib):
+    from paper_2309_08038_gb300 import _lib as L
+    rad = L.RadarStruct(77e9, 1e14, 1e-7, 8e-6, 0.25, 0.0)
+    b = lib.rosar_bpa_time
+    assert b(FAKE, None, ctypes.byref(rad), 360, 24, 64, 60, FAKE2, None) == 2           # L % 16 != 0
+    assert b(FAKE, None, ctypes.byref(rad), 360, 8, 64, 60, FAKE2, None) == 1            # L < 16
+    assert b(FAKE, None, ctypes.byref(rad), 360, 64, 64, 361, FAKE2, None) == 1          # M_ap > n_az
+    assert b(ctypes.c_void_p(0x10008), None, ctypes.byref(rad), 360, 64, 64, 60, FAKE2, None) == 1   # raw not 16-B
+    assert b(FAKE, None, None, 360, 64, 64, 60, FAKE2, None) == 1
+    assert b(FAKE, None, ctypes.byref(rad), 360, 64, 64, 60, FAKE, None) == 1            # out aliases raw
+    f = lib.rosar_sas_time
+    assert f(FAKE, None, FAKE, FAKE, 0, ctypes.byref(rad), 360, 64, 64, 16, 2, FAKE2, None) == 1    # centred
+    assert f(FAKE, None, FAKE, FAKE, 5, ctypes.byref(rad), 360, 64, 64, 16, 1, FAKE2, None) == 1    # stride < K
+    assert f(FAKE, None, None, FAKE, 0, ctypes.byref(rad), 360, 64, 64, 16, 1, FAKE2, None) == 1
+    assert f(FAKE, None, FAKE, FAKE, 0, ctypes.byref(rad), 360, 40, 64, 16, 1, FAKE2, None) == 2    # L % 16
+    assert f(FAKE, None, FAKE, FAKE, 0, ctypes.byref(rad), 360, 64, 64, 0, 1, FAKE2, None) == 1     # K = 0
+
+
 def test_image_rejects_bad_arguments(lib):
     f = lib.rosar_image
     assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2
