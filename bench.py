@@ -518,9 +518,13 @@ def run_ours(args):
             "sas_time_px_s": world * px / t_st,
             "time_domain_kernels": {
                 "td_tile_kernel<BPA>": {"us_per_launch": t_bt * 1e6, "algorithmic_flops": f_bt,
-                                        "tflops": f_bt / t_bt / 1e12, "alu_frac": f_bt / t_bt / 1e12 / fp32_peak},
+                                        "tflops": f_bt / t_bt / 1e12, "alu_frac": f_bt / t_bt / 1e12 / fp32_peak,
+                                        "traffic": recorded_traffic("td_tile_kernel<1>", "indoor",
+                                                                    source_hash("time_domain.cu"))},
                 "td_tile_kernel<SAS>": {"us_per_launch": t_st * 1e6, "algorithmic_flops": f_st,
-                                        "tflops": f_st / t_st / 1e12, "alu_frac": f_st / t_st / 1e12 / fp32_peak}},
+                                        "tflops": f_st / t_st / 1e12, "alu_frac": f_st / t_st / 1e12 / fp32_peak,
+                                        "traffic": recorded_traffic("td_tile_kernel<0>", "indoor",
+                                                                    source_hash("time_domain.cu"))}},
             "paper_table_ms_per_image": {"BPA": t_bt * 1e3, "SAS": t_st * 1e3, "FFT+BPA": t_bn * 1e3,
                                          "FFT+SAS": ms_step},
             "note": "FFT+BPA = range compression + back-projection over the same M=600 pulses with the "
