@@ -159,6 +159,26 @@ ROSAR_API rosar_status rosar_image_migrating(const rosar_c32 *raw, const float *
                                              const int32_t *o, int o_row_stride, const int32_t *dl, int n_az, int L,
                                              int K, rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
+/*
+ * rosar_image_fft with the raw cube and the image in HOST memory: on `stream` it copies
+ * raw_host into raw_dev (cudaMemcpyAsync), runs rosar_image_fft into out_dev and copies
+ * the image back into out_host.  The call returns once the work is enqueued; out_host holds
+ * the image after the stream has been synchronised.  Host buffers should be page-locked
+ * (cudaHostAlloc or registered) so the copies run asynchronously and overlap work on other
+ * streams; pageable buffers work but make the copies synchronous.  A caller pipelines scans
+ * by giving each call in flight its own stream and device buffers.  The paper has no
+ * counterpart (it is the I/O of one imaging step).
+ *   raw_host  [n_az][L] complex, host (in)     raw_dev   [n_az][L] device staging (scratch)
+ *   win, H    as rosar_image_fft (device, in)  workspace [L][n_az] device (scratch)
+ *   out_dev   [L][n_az] device (out: the image, as rosar_image_fft)
+ *   out_host  [L][n_az] complex, host (out)
+ * Errors: argument errors before anything is enqueued; a failed copy or launch returns
+ * ROSAR_ERR_CUDA (work enqueued before it may still run).
+ */
+ROSAR_API rosar_status rosar_image_fft_host(const rosar_c32 *raw_host, const float *win, const rosar_c32 *H,
+                                            int n_az, int L, rosar_c32 *raw_dev, rosar_c32 *workspace,
+                                            rosar_c32 *out_dev, rosar_c32 *out_host, void *stream);
+
 /* ------------------------------------------------------------------------
  * Time-domain comparison paths: the paper's "BPA" (Sec. II-C, Eq. (14)) and
  * "SAS" (Sec. III-A, Algorithm 2 with W_SA).  Both read the raw IF cube and

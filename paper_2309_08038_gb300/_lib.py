@@ -51,6 +51,7 @@ _PROTOS = {
     "rosar_sparse_azimuth": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_image_fft_host": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "rosar_bpa_time": (_I, [_P, _P, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _P, _P]),
     "rosar_sas_time": (_I, [_P, _P, _P, _P, _I, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),

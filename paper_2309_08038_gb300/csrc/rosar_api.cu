@@ -298,6 +298,38 @@ rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar
                               n_az, reinterpret_cast<float2 *>(out), s, true);
 }
 
+rosar_status rosar_image_fft_host(const rosar_c32 *raw_host, const float *win, const rosar_c32 *H, int n_az, int L,
+                                  rosar_c32 *raw_dev, rosar_c32 *workspace, rosar_c32 *out_dev, rosar_c32 *out_host,
+                                  void *stream) {
+    clear_error();
+    if (!raw_host || !out_host) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_host: null host buffer");
+    rosar_status st = check_range_args(raw_dev, win, n_az, L, workspace);
+    if (st != ROSAR_OK) return st;
+    if (!H || !out_dev) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_host: null H or out_dev");
+    if (misaligned(H, 8) || misaligned(out_dev, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_host: misaligned pointer");
+    const size_t bytes = sizeof(rosar_c32) * (size_t)n_az * L;
+    if (overlaps(out_dev, bytes, workspace, bytes) || overlaps(out_dev, bytes, raw_dev, bytes) ||
+        overlaps(out_dev, bytes, H, bytes) || overlaps(raw_dev, bytes, workspace, bytes))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_host: device buffers overlap");
+    if (overlaps(raw_host, bytes, out_host, bytes))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_host: host buffers overlap");
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "image_fft_host: n_az=%d is not 2^a 3^b 5^c <= 16384", n_az);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(raw_dev, raw_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "image_fft_host: H2D copy: %s", cudaGetErrorString(e));
+    st = launch_range_compress(reinterpret_cast<const float2 *>(raw_dev), win, n_az, L, 1,
+                               reinterpret_cast<float2 *>(workspace), s);
+    if (st != ROSAR_OK) return st;
+    st = launch_azimuth_fft(reinterpret_cast<const float2 *>(workspace), reinterpret_cast<const float2 *>(H), L, n_az,
+                            reinterpret_cast<float2 *>(out_dev), s, true);
+    if (st != ROSAR_OK) return st;
+    e = cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "image_fft_host: D2H copy: %s", cudaGetErrorString(e));
+    return ROSAR_OK;
+}
+
 // ------------------------------------------------------------ differentiable form --
 
 namespace {

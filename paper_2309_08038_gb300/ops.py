@@ -98,6 +98,33 @@ def bpa(S, radar: Radar, n_rng, M_ap, interp="linear", dphi=None, dr=None, out=N
     return out
 
 
+def image_fft_host(raw_host, win, H, raw_dev, workspace, out_dev, out_host, stream=None):
+    """rosar_image_fft_host: raw_host (CPU tensor, page-locked for asynchronous copies) -> H2D into raw_dev,
+    range compression + frequency-domain azimuth filter into out_dev, D2H into out_host (CPU tensor), all
+    enqueued on `stream`; out_host is valid once the stream is synchronised."""
+    import torch
+    lib = _lib.load()
+    if not isinstance(raw_host, torch.Tensor) or raw_host.is_cuda or not isinstance(out_host, torch.Tensor) or \
+            out_host.is_cuda:
+        raise ValueError("raw_host and out_host must be CPU tensors")
+    if raw_host.dtype != torch.complex64 or out_host.dtype != torch.complex64 or raw_host.dim() != 2 or \
+            not raw_host.is_contiguous() or not out_host.is_contiguous():
+        raise ValueError("raw_host and out_host must be contiguous complex64 matrices")
+    n_az, L = raw_host.shape
+    if tuple(out_host.shape) != (L, n_az):
+        raise ValueError(f"out_host must have shape ({L}, {n_az})")
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(H, torch.complex64, "H", shape=(L, n_az))
+    require(raw_dev, torch.complex64, "raw_dev", shape=(n_az, L))
+    require(workspace, torch.complex64, "workspace", shape=(L, n_az))
+    require(out_dev, torch.complex64, "out_dev", shape=(L, n_az))
+    check(lib.rosar_image_fft_host(ctypes.c_void_p(raw_host.data_ptr()), ptr(win), ptr(H), n_az, L, ptr(raw_dev),
+                                   ptr(workspace), ptr(out_dev), ctypes.c_void_p(out_host.data_ptr()),
+                                   stream_handle(stream)))
+    return out_host
+
+
 def bpa_time(raw, win, radar: Radar, n_rng, M_ap, out=None, stream=None):
     """rosar_bpa_time: time-domain back-projection (Eq. (14)) of the raw cube [n_az, L] onto rows 0..n_rng-1."""
     lib = _lib.load()

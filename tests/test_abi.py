@@ -99,6 +99,19 @@ def test_time_domain_rejects_bad_arguments(lib):
     assert f(FAKE, None, FAKE, FAKE, 0, ctypes.byref(rad), 360, 64, 64, 0, 1, FAKE2, None) == 1     # K = 0
 
 
+def test_image_fft_host_rejects_bad_arguments(lib):
+    f = lib.rosar_image_fft_host
+    hr, ho = ctypes.c_void_p(0x70000000), ctypes.c_void_p(0x78000000)
+    ws, od = ctypes.c_void_p(0x40000000), ctypes.c_void_p(0x48000000)
+    assert f(None, None, FAKE2, 360, 64, FAKE, ws, od, ho, None) == 1          # no host input
+    assert f(hr, None, FAKE2, 360, 64, FAKE, ws, od, None, None) == 1          # no host output
+    assert f(hr, None, None, 360, 64, FAKE, ws, od, ho, None) == 1             # no plan
+    assert f(hr, None, FAKE2, 360, 48, FAKE, ws, od, ho, None) == 2            # L not a power of two
+    assert f(hr, None, FAKE2, 7 * 360, 64, FAKE, ws, od, ho, None) == 2        # n_az has a factor 7
+    assert f(hr, None, FAKE2, 360, 64, FAKE, ws, ws, ho, None) == 1            # out_dev aliases workspace
+    assert f(hr, None, FAKE2, 360, 64, FAKE, ws, od, hr, None) == 1            # host buffers alias
+
+
 def test_image_rejects_bad_arguments(lib):
     f = lib.rosar_image
     assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2

@@ -124,3 +124,34 @@ def test_unsupported_length_is_refused(rosar):
     o = torch.zeros(3, dtype=torch.int32, device="cuda")
     with pytest.raises(rosar.RosarError, match="UNSUPPORTED"):
         rosar.azimuth_plan(w, o, 7 * 64)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_image_fft_host_equals_device_call(rosar, pinned):
+    """rosar_image_fft_host = H2D copy + rosar_image_fft + D2H copy: the image in host memory is bit for bit
+    the device call's, with page-locked and with pageable host buffers, on a side stream; consecutive calls
+    on three streams with their own buffers give each scan's own image."""
+    import torch
+    cfg = synth.TINY
+    rng = np.random.default_rng(61)
+    o = synth.draw_offsets(cfg)
+    w = torch.from_numpy(synth.default_weights(cfg, o)).cuda()
+    H = rosar.azimuth_plan(w, torch.from_numpy(o).cuda(), cfg.n_az)
+    win = torch.from_numpy(synth.hann_window(cfg.L)).cuda()
+    raws = [_c(rng, cfg.n_az, cfg.L) for _ in range(3)]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    outs_host = []
+    for i, r in enumerate(raws):
+        hr = torch.from_numpy(r)
+        ho = torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64)
+        if pinned:
+            hr, ho = hr.pin_memory(), ho.pin_memory()
+        rd = torch.empty((cfg.n_az, cfg.L), dtype=torch.complex64, device="cuda")
+        ws = torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device="cuda")
+        od = torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device="cuda")
+        rosar.image_fft_host(hr, win, H, rd, ws, od, ho, stream=streams[i])
+        outs_host.append(ho)
+    torch.cuda.synchronize()
+    for r, ho in zip(raws, outs_host):
+        ref = rosar.image_fft(torch.from_numpy(r).cuda(), win, H).cpu()
+        assert torch.equal(ho, ref)
