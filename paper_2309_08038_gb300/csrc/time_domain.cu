@@ -25,17 +25,32 @@
 //
 // Compute-bound on FP32 FMA: 8 flops per (pixel, tap, sample).
 
+#include <cooperative_groups.h>
+
+#include <cmath>
+
 #include "rosar_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rosar {
 namespace {
 
-constexpr int TD_THREADS = 256;
+constexpr int TD_THREADS = 128;
 constexpr int TD_BT = 128;   // azimuth pixels per CTA
 constexpr int TD_BR = 32;    // range rows per CTA (= warp size: one table entry per lane of warp 0)
 constexpr int TD_MC = 16;    // fast-time samples per stage
-constexpr int TD_TQ = TD_BT / 32;                 // azimuth pixels per thread (4)
-constexpr int TD_TI = TD_BR / (TD_THREADS / 32);  // rows per thread (4)
+constexpr int TD_AS = TD_MC + 1;                  // A row stride in elements (odd: conflict-free column reads)
+constexpr int TD_TQ = TD_BT / 32;                 // azimuth pixels per thread (4): lane + 32 q
+constexpr int TD_TI = TD_BR / (TD_THREADS / 32);  // rows per thread (8): 8 * warp + i
+constexpr int TD_MAX_CLUSTER = 8;
+
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // (c.re, c.im, phi_hi, phi_lo) of tap offset o in row r; c is only filled for BPA.
 template <bool BPA>
@@ -75,11 +90,14 @@ __device__ __forceinline__ float2 phasor_term(float4 t, float wm, float x) {
     return cmul(c, make_float2(cs, -sn));
 }
 
+// One CTA = TD_BT pixels x TD_BR rows x the taps [k_lo, k_hi) of its cluster rank.  With a cluster of G > 1
+// CTAs along z the taps are split in G contiguous ranges and rank 0 adds the other ranks' partial tiles,
+// read from their shared memory, in rank order (deterministic).
 template <bool BPA>
-__global__ void __launch_bounds__(TD_THREADS, 2)
+__global__ void __launch_bounds__(TD_THREADS, 4)
 td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
-               const int32_t *__restrict__ o, TdParams p, int K, float2 *__restrict__ out) {
-    __shared__ __align__(16) float2 As[2][TD_MC][TD_BT];
+               const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
+    __shared__ __align__(16) float2 As[2][TD_BT * TD_AS];
     __shared__ __align__(16) float2 Bs[2][TD_MC][TD_BR];
     __shared__ float4 tab[3][TD_BR];
 
@@ -87,71 +105,52 @@ td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, cons
     const int th0 = blockIdx.x * TD_BT, r0 = blockIdx.y * TD_BR;
     const int n_az = p.n_az, L = p.L;
     const int chunks = L / TD_MC;
-    const int stages = K * chunks;
+    const int k_lo = blockIdx.z * k_per;
+    const int nk = max(0, min(K, k_lo + k_per) - k_lo);
+    const int stages = nk * chunks;
+    const bool wide = n_az >= TD_BT;            // one conditional subtraction wraps a tile row index
 
-    auto tap_off = [&](int k) -> int { return BPA ? k - K / 2 : pmod(__ldg(o + k), n_az); };
-    auto build_tab = [&](int k) {               // warp 0: one row per lane
+    auto tap_off = [&](int kk) -> int {
+        const int k = k_lo + kk;
+        return BPA ? k - K / 2 : pmod(__ldg(o + k), n_az);
+    };
+    auto build_tab = [&](int kk) {              // warp 0: one row per lane
         const int r = r0 + lane;
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < p.n_rng) {
-            t = tap_entry<BPA>(p, r, tap_off(k));
+            t = tap_entry<BPA>(p, r, tap_off(kk));
             if (!BPA) {
-                const float2 c = __ldg(w + (size_t)r * K + k);
+                const float2 c = __ldg(w + (size_t)r * K + k_lo + kk);
                 t.x = c.x;
                 t.y = c.y;
             }
         }
-        tab[k % 3][lane] = t;
+        tab[kk % 3][lane] = t;
     };
-
-    float4 areg[4];
-    float2 breg[2];
-    auto load_A = [&](int s) {
-        const int k = s / chunks, m0 = (s - k * chunks) * TD_MC;
-        const int off = tap_off(k);
+    auto load_A = [&](int s, int buf) {         // 128 pulses x 16 samples by 8-byte cp.async, transposed rows
+        const int kk = s / chunks, m0 = (s - kk * chunks) * TD_MC;
+        const int base = pmod(th0 + tap_off(kk), n_az);
+        const int m = tid & (TD_MC - 1);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int u = tid + TD_THREADS * q;
-            const int t = u & (TD_BT - 1), c = u >> 7;
-            const int row = pmod(th0 + off + t, n_az);
-            const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)row * L + m0 + 4 * c);
-            areg[2 * q] = __ldg(src);
-            areg[2 * q + 1] = __ldg(src + 1);
+        for (int j = 0; j < TD_BT * TD_MC / TD_THREADS; ++j) {
+            const int t = (tid >> 4) + j * (TD_THREADS / TD_MC);
+            int row = base + t;
+            if (wide) row = row >= n_az ? row - n_az : row;
+            else row %= n_az;
+            cp_async8(&As[buf][t * TD_AS + m], X + (size_t)row * L + m0 + m);
         }
+        cp_async_commit();
     };
-    auto gen_B = [&](int s) {
-        const int k = s / chunks, m0 = (s - k * chunks) * TD_MC;
+    auto gen_B = [&](int s, int buf) {
+        const int kk = s / chunks, m0 = (s - kk * chunks) * TD_MC;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < TD_BR * TD_MC / TD_THREADS; ++q) {
             const int v = tid + TD_THREADS * q;
             const int j = v & (TD_BR - 1), m = v >> 5;
             const float wm = win ? __ldg(win + m0 + m) : 1.f;
-            breg[q] = phasor_term(tab[k % 3][j], wm, (float)(m0 + m) - p.m_ref);
+            Bs[buf][m][j] = phasor_term(tab[kk % 3][j], wm, (float)(m0 + m) - p.m_ref);
         }
     };
-    auto store = [&](int buf) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int u = tid + TD_THREADS * q;
-            const int t = u & (TD_BT - 1), c = u >> 7;
-            As[buf][4 * c + 0][t] = make_float2(areg[2 * q].x, areg[2 * q].y);
-            As[buf][4 * c + 1][t] = make_float2(areg[2 * q].z, areg[2 * q].w);
-            As[buf][4 * c + 2][t] = make_float2(areg[2 * q + 1].x, areg[2 * q + 1].y);
-            As[buf][4 * c + 3][t] = make_float2(areg[2 * q + 1].z, areg[2 * q + 1].w);
-            const int v = tid + TD_THREADS * q;
-            Bs[buf][v >> 5][v & (TD_BR - 1)] = breg[q];
-        }
-    };
-
-    if (warp == 0) {
-        build_tab(0);
-        if (K > 1) build_tab(1);
-    }
-    __syncthreads();
-    load_A(0);
-    gen_B(0);
-    store(0);
-    __syncthreads();
 
     float2 acc[TD_TQ][TD_TI];
 #pragma unroll
@@ -159,36 +158,74 @@ td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, cons
 #pragma unroll
         for (int i = 0; i < TD_TI; ++i) acc[q][i] = make_float2(0.f, 0.f);
 
+    if (stages > 0) {
+        if (warp == 0) {
+            build_tab(0);
+            if (nk > 1) build_tab(1);
+        }
+        load_A(0, 0);
+        __syncthreads();
+        gen_B(0, 0);
+        cp_async_wait_all();
+        __syncthreads();
+    }
     for (int s = 0; s < stages; ++s) {
         const int buf = s & 1;
         const bool more = s + 1 < stages;
-        if (more) load_A(s + 1);
+        if (more) load_A(s + 1, buf ^ 1);
         if (warp == 0 && s % chunks == 0) {
-            const int k = s / chunks + 2;
-            if (k < K) build_tab(k);
+            const int kk = s / chunks + 2;
+            if (kk < nk) build_tab(kk);
         }
+        const float2 *arow = &As[buf][lane * TD_AS];
 #pragma unroll
         for (int m = 0; m < TD_MC; ++m) {
             float2 a[TD_TQ], b[TD_TI];
 #pragma unroll
-            for (int q = 0; q < TD_TQ; ++q) a[q] = As[buf][m][lane + 32 * q];
+            for (int q = 0; q < TD_TQ; ++q) a[q] = arow[32 * q * TD_AS + m];
+            const float4 *bp = reinterpret_cast<const float4 *>(&Bs[buf][m][TD_TI * warp]);
 #pragma unroll
-            for (int i = 0; i < TD_TI; ++i) b[i] = Bs[buf][m][warp + 8 * i];
+            for (int i = 0; i < TD_TI / 2; ++i) {
+                const float4 v = bp[i];
+                b[2 * i] = make_float2(v.x, v.y);
+                b[2 * i + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
             for (int q = 0; q < TD_TQ; ++q)
 #pragma unroll
                 for (int i = 0; i < TD_TI; ++i) cmac(acc[q][i], a[q], b[i]);
         }
-        if (more) {
-            gen_B(s + 1);
-            store(buf ^ 1);
-        }
+        if (more) gen_B(s + 1, buf ^ 1);
+        cp_async_wait_all();
         __syncthreads();
     }
 
+    // cluster split: every rank parks its partial tile in its own shared memory, rank 0 adds them in order
+    const int G = gridDim.z;
+    if (G > 1) {
+        float2 *red = &As[0][0];                // 32 * 128 float2 = 32 KB <= sizeof(As)
+        cg::cluster_group cluster = cg::this_cluster();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TD_TQ; ++q)
+#pragma unroll
+            for (int i = 0; i < TD_TI; ++i) red[(q * TD_TI + i) * TD_THREADS + tid] = acc[q][i];
+        cluster.sync();
+        if (cluster.block_rank() == 0) {
+            for (int rk = 1; rk < G; ++rk) {
+                const float2 *rem = cluster.map_shared_rank(red, rk);
+#pragma unroll
+                for (int q = 0; q < TD_TQ; ++q)
+#pragma unroll
+                    for (int i = 0; i < TD_TI; ++i) acc[q][i] = cadd(acc[q][i], rem[(q * TD_TI + i) * TD_THREADS + tid]);
+            }
+        }
+        cluster.sync();                         // the other ranks keep their shared memory until rank 0 is done
+        if (cluster.block_rank() != 0) return;
+    }
 #pragma unroll
     for (int i = 0; i < TD_TI; ++i) {
-        const int r = r0 + warp + 8 * i;
+        const int r = r0 + TD_TI * warp + i;
         if (r >= p.n_rng) continue;
 #pragma unroll
         for (int q = 0; q < TD_TQ; ++q) {
@@ -271,6 +308,70 @@ td_row_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
     }
 }
 
+// Cluster size for the tap split: the G (1 .. 8, at most K, at least 8 taps per rank unless G = 1) whose
+// clusters fill the co-resident cluster slots in the most nearly whole number of waves.
+template <bool BPA>
+int pick_cluster(int tiles, int K) {
+    static int cached_dev = -1, cached_tiles = -1, cached_K = -1, cached_G = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev == cached_dev && tiles == cached_tiles && K == cached_K) return cached_G;
+    int best_G = 1;
+    double best = -1.0;
+    for (int G = 1; G <= TD_MAX_CLUSTER; ++G) {
+        if (G > 1 && (K < 8 * G)) break;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(1, 1, G);
+        cfg.blockDim = dim3(TD_THREADS);
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = G;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, td_tile_kernel<BPA>, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const double waves = (double)tiles / clusters;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best + 1e-3) {
+            best = eff;
+            best_G = G;
+        }
+    }
+    cached_dev = dev;
+    cached_tiles = tiles;
+    cached_K = K;
+    cached_G = best_G;
+    return best_G;
+}
+
+template <bool BPA>
+rosar_status launch_tiles(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p,
+                          int K, float2 *out, cudaStream_t s) {
+    const int gx = (p.n_az + TD_BT - 1) / TD_BT, gy = (p.n_rng + TD_BR - 1) / TD_BR;
+    const int G = pick_cluster<BPA>(gx * gy, K);
+    const int k_per = (K + G - 1) / G;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(gx, gy, G);
+    cfg.blockDim = dim3(TD_THREADS);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = G;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tile_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
+    if (e != cudaSuccess)
+        return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", BPA ? "bpa_time" : "sas_time", cudaGetErrorString(e));
+    return check_launch(BPA ? "bpa_time" : "sas_time");
+}
+
 }  // namespace
 
 int time_domain_sample_multiple() { return TD_MC; }
@@ -279,14 +380,9 @@ rosar_status launch_time_domain(const float2 *raw, const float *win, const float
                                 int o_row_stride, const TdParams &p, int K, bool bpa, float2 *out, cudaStream_t s) {
     if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: L=%d is not a multiple of %d", p.L, TD_MC);
     if (bpa || o_row_stride == 0) {
-        const int gy = (p.n_rng + TD_BR - 1) / TD_BR;
-        if (gy > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
-        dim3 grid((p.n_az + TD_BT - 1) / TD_BT, gy);
-        if (bpa)
-            td_tile_kernel<true><<<grid, TD_THREADS, 0, s>>>(raw, win, w, o, p, K, out);
-        else
-            td_tile_kernel<false><<<grid, TD_THREADS, 0, s>>>(raw, win, w, o, p, K, out);
-        return check_launch(bpa ? "bpa_time" : "sas_time");
+        if ((p.n_rng + TD_BR - 1) / TD_BR > 65535)
+            return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
+        return bpa ? launch_tiles<true>(raw, win, w, o, p, K, out, s) : launch_tiles<false>(raw, win, w, o, p, K, out, s);
     }
     if (p.n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
     dim3 grid((p.n_az + TR_BT - 1) / TR_BT, p.n_rng);
