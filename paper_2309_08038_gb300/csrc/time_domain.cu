@@ -178,7 +178,7 @@ td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, cons
             if (kk < nk) build_tab(kk);
         }
         const float2 *arow = &As[buf][lane * TD_AS];
-#pragma unroll
+#pragma unroll 4                                 // full unrolling overflows the instruction cache
         for (int m = 0; m < TD_MC; ++m) {
             float2 a[TD_TQ], b[TD_TI];
 #pragma unroll
