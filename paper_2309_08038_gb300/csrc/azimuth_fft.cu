@@ -35,10 +35,11 @@ struct Layout {
     size_t bytes;
 };
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
-azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, RowPlan pl, Layout lay,
-                   float2 *__restrict__ out) {
+// The row filter on one CTA: stage the H row and the twiddle table, wait for S, forward DIF, product with
+// H (digit-reversed order, carries 1/N) between conjugations, DIT, store.  FWD/DIT run the passes.
+template <typename FWD, typename INV>
+__device__ __forceinline__ void row_filter(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, int pad_shift,
+                                           const Layout &lay, float2 *__restrict__ out, FWD fwd, INV inv) {
     extern __shared__ float2 sm[];
     float2 *x = sm;
     float2 *hb = x + padded_len(N);
@@ -46,34 +47,52 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
     const size_t row = (size_t)blockIdx.x * N;
     // prologue independent of S: the H row and the twiddle table
     if (lay.stage_h)
-        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + rpad(n, pl.pad_shift), H + row + n);
+        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + rpad(n, pad_shift), H + row + n);
     cp_async_commit();
     const float2 *tc, *tf;
     build_twiddles(N, lay.full_tab != 0, tw, &tc, &tf);
     griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
-    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + rpad(n, pl.pad_shift), S + row + n);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + rpad(n, pad_shift), S + row + n);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    row_dif(x, N, pl, tc, tf);
+    fwd(x, tc, tf);
     if (lay.stage_h) {
         for (int n = threadIdx.x; n < N; n += blockDim.x) {   // spectrum times H (same digit-reversed order, carries 1/N), conjugated
-            const float2 y = cmul(hb[rpad(n, pl.pad_shift)], x[rpad(n, pl.pad_shift)]);
-            x[rpad(n, pl.pad_shift)] = make_float2(y.x, -y.y);
+            const float2 y = cmul(hb[rpad(n, pad_shift)], x[rpad(n, pad_shift)]);
+            x[rpad(n, pad_shift)] = make_float2(y.x, -y.y);
         }
     } else {
 #pragma unroll 4
         for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            const float2 y = cmul(__ldg(H + row + n), x[rpad(n, pl.pad_shift)]);
-            x[rpad(n, pl.pad_shift)] = make_float2(y.x, -y.y);
+            const float2 y = cmul(__ldg(H + row + n), x[rpad(n, pad_shift)]);
+            x[rpad(n, pad_shift)] = make_float2(y.x, -y.y);
         }
     }
     __syncthreads();
-    row_dit(x, N, pl, tc, tf);
+    inv(x, tc, tf);
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const float2 y = x[rpad(n, pl.pad_shift)];
+        const float2 y = x[rpad(n, pad_shift)];
         out[row + n] = make_float2(y.x, -y.y);
     }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
+azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, RowPlan pl, Layout lay,
+                   float2 *__restrict__ out) {
+    row_filter(S, H, N, pl.pad_shift, lay, out,
+               [&](float2 *x, const float2 *tc, const float2 *tf) { row_dif(x, N, pl, tc, tf); },
+               [&](float2 *x, const float2 *tc, const float2 *tf) { row_dit(x, N, pl, tc, tf); });
+}
+
+// Compile-time plan for one row length (T threads, no padding: N has an odd factor).
+template <int T, int N, int... R>
+__global__ void __launch_bounds__(T, 1)
+azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, Layout lay, float2 *__restrict__ out) {
+    row_filter(S, H, N, pad_shift_for(N), lay, out,
+               [](float2 *x, const float2 *tc, const float2 *tf) { dif_seq<N, N, false, T, R...>(x, tc, tf); },
+               [](float2 *x, const float2 *tc, const float2 *tf) { dit_seq<N, N, false, T, R...>(x, tc, tf); });
 }
 
 template <int MAXT>
@@ -150,6 +169,40 @@ cudaError_t launch_fft_rows(int g, int t, size_t sm, cudaStream_t s, bool overla
     return cudaLaunchKernelEx(&cfg, azimuth_fft_kernel<MAXT>, S, H, N, pl, lay, out);
 }
 
+namespace {
+
+// Launches the compile-time-plan kernel when the run-time planner picks exactly its radices for n_az (so H,
+// made by the run-time plan, is in the same order); returns false to fall back to the run-time plan.
+template <int N, int... R>
+bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, bool ov, const float2 *S, const float2 *H,
+               float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
+    constexpr int T = 256;
+    constexpr int rad[] = {R...};
+    if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pl.npass != (int)sizeof...(R))
+        return false;
+    for (int i = 0; i < pl.npass; ++i)
+        if (pl.rad[i] != rad[i]) return false;
+    static int done[kMaxDevices] = {};
+    const void *k = (const void *)azimuth_fft_fixed_kernel<T, N, R...>;
+    *st = ensure_smem(k, lay.bytes, done, "azimuth_fft");
+    if (*st != ROSAR_OK) return true;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_rng);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = lay.bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = ov ? 1 : 0;
+    *le = cudaLaunchKernelEx(&cfg, azimuth_fft_fixed_kernel<T, N, R...>, S, H, lay, out);
+    *st = check_launch("azimuth_fft");
+    return true;
+}
+
+}  // namespace
+
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
                                 bool overlap_predecessor) {
     RowPlan pl;
@@ -158,6 +211,17 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     static int done[4][kMaxDevices] = {};
     const Layout lay = layout_for(n_az, true);
     const bool ov = overlap_predecessor;
+    {
+        cudaError_t fle = cudaSuccess;
+        rosar_status fst = ROSAR_OK;
+        if (try_fixed<3600, 16, 5, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<1800, 8, 5, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<360, 8, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst)) {
+            if (fst == ROSAR_OK && fle != cudaSuccess)
+                return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(fle));
+            return fst;
+        }
+    }
     cudaError_t le = cudaSuccess;
     static const void *const ks[4] = {(const void *)azimuth_fft_kernel<256>, (const void *)azimuth_fft_kernel<384>,
                                       (const void *)azimuth_fft_kernel<512>, (const void *)azimuth_fft_kernel<1024>};

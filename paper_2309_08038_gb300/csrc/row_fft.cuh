@@ -182,6 +182,66 @@ __device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const floa
 }
 #undef ROSAR_STAGE_CASE
 
+// Compile-time plans: the same passes for a row length N and a radix sequence fixed at compile time, run by
+// exactly T threads.  Strides, block counts and the quotient by the stride become constants and the
+// per-pass radix dispatch disappears; results are identical to the run-time plan with the same radices.
+template <int... R>
+struct Radices {};
+
+template <int N, int M, int R, bool PAD, int T>
+__device__ __forceinline__ void dif_pass_c(float2 *x, const float2 *tc, const float2 *tf) {
+    constexpr int s = M / R, tstep = N / M, nb = N / R;
+#pragma unroll 1
+    for (int idx = threadIdx.x; idx < nb; idx += T) {
+        const int blk = idx / s, j = idx - blk * s;
+        const int base = blk * M + j;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[cpad<PAD>(base + r * s)];
+        small_dft<R>(v);
+        x[cpad<PAD>(base)] = v[0];
+        float2 wq[R];
+        twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[cpad<PAD>(base + q * s)] = cmul(v[q], wq[q]);
+    }
+    __syncthreads();
+}
+
+template <int N, int M, int R, bool PAD, int T>
+__device__ __forceinline__ void dit_pass_c(float2 *x, const float2 *tc, const float2 *tf) {
+    constexpr int s = M / R, tstep = N / M, nb = N / R;
+#pragma unroll 1
+    for (int idx = threadIdx.x; idx < nb; idx += T) {
+        const int blk = idx / s, j = idx - blk * s;
+        const int base = blk * M + j;
+        float2 v[R];
+        float2 wq[R];
+        twiddle_powers<R>(twiddle(j * tstep, tc, tf), wq);
+        v[0] = x[cpad<PAD>(base)];
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmul(x[cpad<PAD>(base + q * s)], wq[q]);
+        small_dft<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[cpad<PAD>(base + r * s)] = v[r];
+    }
+    __syncthreads();
+}
+
+// DIF passes in plan order, the block length M shrinking by each radix.
+template <int N, int M, bool PAD, int T, int R, int... Rest>
+__device__ __forceinline__ void dif_seq(float2 *x, const float2 *tc, const float2 *tf) {
+    dif_pass_c<N, M, R, PAD, T>(x, tc, tf);
+    if constexpr (sizeof...(Rest) > 0) dif_seq<N, M / R, PAD, T, Rest...>(x, tc, tf);
+}
+
+// DIT passes in reverse plan order: the last radix first (M = that radix), the first radix last (M = N).
+template <int N, int M, bool PAD, int T, int R, int... Rest>
+__device__ __forceinline__ void dit_seq(float2 *x, const float2 *tc, const float2 *tf) {
+    if constexpr (sizeof...(Rest) > 0) dit_seq<N, M / R, PAD, T, Rest...>(x, tc, tf);
+    dit_pass_c<N, M, R, PAD, T>(x, tc, tf);
+}
+
 // Forward DFT of the row, output in digit-reversed order.
 template <bool PAD>
 __device__ __forceinline__ void row_dif_t(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
