@@ -34,6 +34,7 @@ struct ScanDev {
     const float2 *H;          // frequency-domain plan [L][n_az], or null: gather tiles
     int o_row_stride, n_az, L, K;
     int range_tiles, az_tiles_per_row, P, vec_store;
+    int fixed;                // compile-time plan of the row FFT (1: 1800, 2: 3600, 3: 7200 pulses), 0: run-time plan
     rowfft::RowPlan plan;
 };
 
@@ -90,13 +91,23 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
         }
     }
     __syncthreads();
-    rowfft::row_dif(x, N, sc.plan, tc, tf);
+    switch (sc.fixed) {                       // same passes as the run-time plan, constant strides
+        case 1: rowfft::dif_seq<1800, 1800, false, BT_THREADS, 8, 5, 5, 3, 3>(x, tc, tf); break;
+        case 2: rowfft::dif_seq<3600, 3600, false, BT_THREADS, 16, 5, 5, 3, 3>(x, tc, tf); break;
+        case 3: rowfft::dif_seq<7200, 7200, false, BT_THREADS, 8, 4, 5, 5, 3, 3>(x, tc, tf); break;
+        default: rowfft::row_dif(x, N, sc.plan, tc, tf);
+    }
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
         const float2 y = cmul(__ldg(sc.H + row + n), x[rowfft::rpad(n, sc.plan.pad_shift)]);
         x[rowfft::rpad(n, sc.plan.pad_shift)] = make_float2(y.x, -y.y);
     }
     __syncthreads();
-    rowfft::row_dit(x, N, sc.plan, tc, tf);
+    switch (sc.fixed) {
+        case 1: rowfft::dit_seq<1800, 1800, false, BT_THREADS, 8, 5, 5, 3, 3>(x, tc, tf); break;
+        case 2: rowfft::dit_seq<3600, 3600, false, BT_THREADS, 16, 5, 5, 3, 3>(x, tc, tf); break;
+        case 3: rowfft::dit_seq<7200, 7200, false, BT_THREADS, 8, 4, 5, 5, 3, 3>(x, tc, tf); break;
+        default: rowfft::row_dit(x, N, sc.plan, tc, tf);
+    }
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
         const float2 y = x[rowfft::rpad(n, sc.plan.pad_shift)];
         sc.out[row + n] = make_float2(y.x, -y.y);
@@ -185,6 +196,17 @@ KernelFn kernel_for(int J) {
         case 8: return batch_kernel<8>;
         default: return batch_kernel<4>;
     }
+}
+
+// The compile-time plans fft_row_tile carries, used only when the run-time planner picks the same radices.
+int fixed_plan_code(int n_az, const rowfft::RowPlan &pl) {
+    static const int r1800[] = {8, 5, 5, 3, 3}, r3600[] = {16, 5, 5, 3, 3}, r7200[] = {8, 4, 5, 5, 3, 3};
+    const int *rad = n_az == 1800 ? r1800 : n_az == 3600 ? r3600 : n_az == 7200 ? r7200 : nullptr;
+    const int np = n_az == 7200 ? 6 : 5;
+    if (!rad || pl.npass != np || pl.pad_shift != rowfft::pad_shift_for(n_az)) return 0;
+    for (int i = 0; i < np; ++i)
+        if (pl.rad[i] != rad[i]) return 0;
+    return n_az == 1800 ? 1 : n_az == 3600 ? 2 : 3;
 }
 
 int g_smem_done[4][kMaxDevices] = {};
@@ -288,6 +310,7 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
                            q.n_az);
             break;
         }
+        d.fixed = q.H ? fixed_plan_code(q.n_az, d.plan) : 0;
         d.o_row_stride = q.o_row_stride;
         d.n_az = q.n_az;
         d.L = q.L;
