@@ -188,12 +188,28 @@ __device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const floa
 template <int... R>
 struct Radices {};
 
+// Butterfly idx of a pass with nblk = N/M blocks of s = M/R butterflies: blocks vary fastest across threads
+// when a warp spans at least 32 blocks (lanes then stride by M, odd after the first pass of an N with an odd
+// factor: distinct banks, and the lanes share one twiddle), else positions within a block vary fastest.
+template <int N, int M, int R>
+__device__ __forceinline__ void butterfly_index(int idx, int &blk, int &j) {
+    constexpr int s = M / R, nblk = N / M;
+    if constexpr (nblk >= 32) {
+        j = idx / nblk;
+        blk = idx - j * nblk;
+    } else {
+        blk = idx / s;
+        j = idx - blk * s;
+    }
+}
+
 template <int N, int M, int R, bool PAD, int T>
 __device__ __forceinline__ void dif_pass_c(float2 *x, const float2 *tc, const float2 *tf) {
     constexpr int s = M / R, tstep = N / M, nb = N / R;
 #pragma unroll 1
     for (int idx = threadIdx.x; idx < nb; idx += T) {
-        const int blk = idx / s, j = idx - blk * s;
+        int blk, j;
+        butterfly_index<N, M, R>(idx, blk, j);
         const int base = blk * M + j;
         float2 v[R];
 #pragma unroll
@@ -213,7 +229,8 @@ __device__ __forceinline__ void dit_pass_c(float2 *x, const float2 *tc, const fl
     constexpr int s = M / R, tstep = N / M, nb = N / R;
 #pragma unroll 1
     for (int idx = threadIdx.x; idx < nb; idx += T) {
-        const int blk = idx / s, j = idx - blk * s;
+        int blk, j;
+        butterfly_index<N, M, R>(idx, blk, j);
         const int base = blk * M + j;
         float2 v[R];
         float2 wq[R];
