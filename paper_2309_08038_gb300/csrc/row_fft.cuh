@@ -127,10 +127,12 @@ using fft::twiddle_powers;
 // v = DFT_R(x[base + r*s]); x[base + q*s] = v[q] * W_M^(j*q).
 template <int R, bool PAD>
 __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
-    const int s = M / R, tstep = N / M, nb = N / R;
-    const float inv_s = 1.f / (float)s;
+    const int s = M / R, tstep = N / M, nb = N / R, nblk = N / M;
+    const bool by_blk = !PAD && nblk >= 32 && (M & 1);     // as butterfly_index: odd lane strides
+    const float inv_d = 1.f / (float)(by_blk ? nblk : s);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        const int blk = quot(idx, inv_s), j = idx - blk * s;
+        const int q = quot(idx, inv_d);
+        const int blk = by_blk ? idx - q * nblk : q, j = by_blk ? q : idx - q * s;
         const int base = blk * M + j;
         float2 v[R];
 #pragma unroll
@@ -148,10 +150,12 @@ __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *
 // The transposed stage (decimation in time): v[q] = x[base + q*s] * W_M^(j*q); x[base + r*s] = DFT_R(v)[r].
 template <int R, bool PAD>
 __device__ __forceinline__ void dit_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
-    const int s = M / R, tstep = N / M, nb = N / R;
-    const float inv_s = 1.f / (float)s;
+    const int s = M / R, tstep = N / M, nb = N / R, nblk = N / M;
+    const bool by_blk = !PAD && nblk >= 32 && (M & 1);     // as butterfly_index: odd lane strides
+    const float inv_d = 1.f / (float)(by_blk ? nblk : s);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        const int blk = quot(idx, inv_s), j = idx - blk * s;
+        const int q = quot(idx, inv_d);
+        const int blk = by_blk ? idx - q * nblk : q, j = by_blk ? q : idx - q * s;
         const int base = blk * M + j;
         float2 v[R];
         float2 wq[R];
@@ -189,12 +193,12 @@ template <int... R>
 struct Radices {};
 
 // Butterfly idx of a pass with nblk = N/M blocks of s = M/R butterflies: blocks vary fastest across threads
-// when a warp spans at least 32 blocks (lanes then stride by M, odd after the first pass of an N with an odd
-// factor: distinct banks, and the lanes share one twiddle), else positions within a block vary fastest.
+// when a warp spans at least 32 blocks of odd length M (lanes then stride by M: distinct banks, and the lanes
+// share one twiddle), else positions within a block vary fastest.
 template <int N, int M, int R>
 __device__ __forceinline__ void butterfly_index(int idx, int &blk, int &j) {
     constexpr int s = M / R, nblk = N / M;
-    if constexpr (nblk >= 32) {
+    if constexpr (nblk >= 32 && (M & 1)) {
         j = idx / nblk;
         blk = idx - j * nblk;
     } else {
