@@ -233,32 +233,39 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_sc
     eps = torch.zeros((n_scans, cfg.n_az), dtype=torch.float32, device=device, requires_grad=True)
     wp = w.clone().requires_grad_(True)
 
-    def forward():
+    def forward(method):
         for s in range(n_scans):
             rosar.range_compress(raws[s], win, out=S_stack[s])
-        return rosar.autograd.sparse_azimuth_phase(S_stack, eps, wp, o)
+        return rosar.autograd.sparse_azimuth_phase(S_stack, eps, wp, o, method=method)
 
-    def fwd_only(i):
-        with torch.no_grad():
-            forward()
+    def timings(method):
+        def fwd_only(i):
+            with torch.no_grad():
+                forward(method)
 
-    def fwd_bwd(i):
-        wp.grad = None
-        eps.grad = None
-        out = forward()
-        loss = torch.sum(torch.abs(out - Bref) ** 2)
-        loss.backward()
+        def fwd_bwd(i):
+            wp.grad = None
+            eps.grad = None
+            out = forward(method)
+            loss = torch.sum(torch.abs(out - Bref) ** 2)
+            loss.backward()
 
-    n = 5
-    ms_f, _ = time_loop(torch, fwd_only, n, 2, stream, world, device)
-    ms_b, _ = time_loop(torch, fwd_bwd, n, 2, stream, world, device)
-    t_f, t_b = ms_f / n * 1e-3, ms_b / n * 1e-3
+        n = 10
+        ms_f, _ = time_loop(torch, fwd_only, n, 3, stream, world, device)
+        ms_b, _ = time_loop(torch, fwd_bwd, n, 3, stream, world, device)
+        return ms_f / n * 1e-3, ms_b / n * 1e-3
+
+    t_f, t_b = timings("auto")
+    t_fg, t_bg = timings("gather")
     pix = n_scans * px
     return {"scans": n_scans, "pixels": pix, "fwd_px_s": world * pix / t_f, "fwd_bwd_px_s": world * pix / t_b,
             "ms_fwd": t_f * 1e3, "ms_fwd_bwd": t_b * 1e3, "bwd_over_fwd": (t_b - t_f) / t_f,
+            "gather_fwd_px_s": world * pix / t_fg, "gather_fwd_bwd_px_s": world * pix / t_bg,
             "grad_finite": bool(torch.isfinite(wp.grad).all().item() and torch.isfinite(eps.grad).all().item()),
-            "note": "step = 16 range compressions + phase-corrected gather filter (forward), torch loss, "
-                    "adjoint gather + weight-gradient + phase-gradient kernels (backward)"}
+            "note": "step = 16 range compressions + phase correction + sparse azimuth filter (forward), torch loss, "
+                    "adjoint filter + weight gradient + phase gradient (backward); default = frequency-domain "
+                    "kernels (plan from w each step, filter with H / conj(H), cross-spectrum weight gradient), "
+                    "gather_* = the gather kernels"}
 
 
 def time_loop(torch, fn, steps, warmup, stream, world, device):

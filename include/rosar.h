@@ -294,6 +294,28 @@ ROSAR_API rosar_status rosar_sparse_azimuth_adjoint(const rosar_c32 *g, const ro
                                                     void *stream);
 
 /*
+ * Frequency-domain form of the differentiable filter (Eq. (43) as a circular
+ * convolution, as rosar_sparse_azimuth_fft), for a stack of scans sharing one plan:
+ *   out[s][r][.] = IFFT(H[r] * FFT(S[s][r][.]))          (adjoint = 0: rosar_sparse_azimuth_scans)
+ *   out[s][r][.] = IFFT(conj(H[r]) * FFT(S[s][r][.]))    (adjoint = 1: grad_S_t of rosar_sparse_azimuth_adjoint)
+ *   S, out [n_scans][n_rng][n_az] (in, out); H [n_rng][n_az] from rosar_azimuth_plan (in).
+ * Limits: n_az = 2^a 3^b 5^c <= 16384; out must not overlap S or H.
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth_fft_scans(const rosar_c32 *S, const rosar_c32 *H, int n_scans, int n_rng,
+                                                      int n_az, int adjoint, rosar_c32 *out, void *stream);
+
+/*
+ * grad_w of rosar_sparse_azimuth_adjoint through the cross-spectrum: per row r,
+ *   corr_r[tau] = sum_s sum_t g[s][r][t] conj(S_t[s][r][(t + tau) mod n_az]) = DFT(sum_s G_s conj(S_s))[tau] / n_az,
+ * with G_s, S_s the rows' transforms, then grad_w[r][k] = corr_r[o_k mod n_az].
+ *   g, S_t [n_scans][n_rng][n_az] (in); o as rosar_sparse_azimuth (in); grad_w [n_rng][K] (out).
+ * Limits: n_az = 2^a 3^b 5^c with three rows of n_az in 200 KB of shared memory (n_az <= 8400 or so).
+ */
+ROSAR_API rosar_status rosar_azimuth_weight_grad_fft(const rosar_c32 *g, const rosar_c32 *S_t, const int32_t *o,
+                                                     int o_row_stride, int n_scans, int n_rng, int n_az, int K,
+                                                     rosar_c32 *grad_w, void *stream);
+
+/*
  * grad_eps[s][n] = sum_r Im(conj(S_t[s][r][n]) * grad_S_t[s][r][n])   (NULL to skip)
  * grad_S[s][r][n] = grad_S_t[s][r][n] * exp(-j*eps[s][n])             (NULL to skip; needs eps)
  */

@@ -52,6 +52,8 @@ _PROTOS = {
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_image_fft_host": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
+    "rosar_sparse_azimuth_fft_scans": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_azimuth_weight_grad_fft": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa_time": (_I, [_P, _P, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _P, _P]),
     "rosar_sas_time": (_I, [_P, _P, _P, _P, _I, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P]),

@@ -37,17 +37,26 @@ struct Layout {
 
 // The row filter on one CTA: stage the H row and the twiddle table, wait for S, forward DIF, product with
 // H (digit-reversed order, carries 1/N) between conjugations, DIT, store.  FWD/DIT run the passes.
+// Row b of S/out uses row (b mod h_rows) of H (a stack of scans sharing one plan); conj_h applies conj(H), the
+// adjoint filter.
+struct RowMap {
+    int h_rows;
+    int conj_h;
+};
+
 template <typename FWD, typename INV>
 __device__ __forceinline__ void row_filter(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, int pad_shift,
-                                           const Layout &lay, float2 *__restrict__ out, FWD fwd, INV inv) {
+                                           const Layout &lay, RowMap map, float2 *__restrict__ out, FWD fwd, INV inv) {
     extern __shared__ float2 sm[];
     float2 *x = sm;
     float2 *hb = x + padded_len(N);
     float2 *tw = lay.stage_h ? hb + padded_len(N) : hb;
     const size_t row = (size_t)blockIdx.x * N;
+    const size_t hrow = (size_t)(blockIdx.x % map.h_rows) * N;
+    const float hs = map.conj_h ? -1.f : 1.f;
     // prologue independent of S: the H row and the twiddle table
     if (lay.stage_h)
-        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + rpad(n, pad_shift), H + row + n);
+        for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(hb + rpad(n, pad_shift), H + hrow + n);
     cp_async_commit();
     const float2 *tc, *tf;
     build_twiddles(N, lay.full_tab != 0, tw, &tc, &tf);
@@ -59,13 +68,17 @@ __device__ __forceinline__ void row_filter(const float2 *__restrict__ S, const f
     fwd(x, tc, tf);
     if (lay.stage_h) {
         for (int n = threadIdx.x; n < N; n += blockDim.x) {   // spectrum times H (same digit-reversed order, carries 1/N), conjugated
-            const float2 y = cmul(hb[rpad(n, pad_shift)], x[rpad(n, pad_shift)]);
+            float2 h = hb[rpad(n, pad_shift)];
+            h.y *= hs;
+            const float2 y = cmul(h, x[rpad(n, pad_shift)]);
             x[rpad(n, pad_shift)] = make_float2(y.x, -y.y);
         }
     } else {
 #pragma unroll 4
         for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            const float2 y = cmul(__ldg(H + row + n), x[rpad(n, pad_shift)]);
+            float2 h = __ldg(H + hrow + n);
+            h.y *= hs;
+            const float2 y = cmul(h, x[rpad(n, pad_shift)]);
             x[rpad(n, pad_shift)] = make_float2(y.x, -y.y);
         }
     }
@@ -79,9 +92,9 @@ __device__ __forceinline__ void row_filter(const float2 *__restrict__ S, const f
 
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
-azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, RowPlan pl, Layout lay,
+azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, int N, RowPlan pl, Layout lay, RowMap map,
                    float2 *__restrict__ out) {
-    row_filter(S, H, N, pl.pad_shift, lay, out,
+    row_filter(S, H, N, pl.pad_shift, lay, map, out,
                [&](float2 *x, const float2 *tc, const float2 *tf) { row_dif(x, N, pl, tc, tf); },
                [&](float2 *x, const float2 *tc, const float2 *tf) { row_dit(x, N, pl, tc, tf); });
 }
@@ -89,8 +102,9 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
 // Compile-time plan for one row length (T threads, no padding: N has an odd factor).
 template <int T, int N, int... R>
 __global__ void __launch_bounds__(T, 1)
-azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, Layout lay, float2 *__restrict__ out) {
-    row_filter(S, H, N, pad_shift_for(N), lay, out,
+azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, Layout lay, RowMap map,
+                         float2 *__restrict__ out) {
+    row_filter(S, H, N, pad_shift_for(N), lay, map, out,
                [](float2 *x, const float2 *tc, const float2 *tf) { dif_seq<N, N, false, T, R...>(x, tc, tf); },
                [](float2 *x, const float2 *tc, const float2 *tf) { dit_seq<N, N, false, T, R...>(x, tc, tf); });
 }
@@ -118,6 +132,54 @@ azimuth_plan_kernel(const float2 *__restrict__ w, const int32_t *__restrict__ o,
     row_dif(x, N, pl, tc, tf);
     const float inv_n = (float)(1.0 / (double)N);
     for (int n = threadIdx.x; n < N; n += blockDim.x) H[(size_t)r * N + n] = cscale(x[rpad(n, pl.pad_shift)], inv_n);
+}
+
+// Weight gradient of the filter for a stack of scans sharing w (the differentiable form), one CTA per row:
+//   corr_r[tau] = sum_s sum_t g[s][r][t] conj(S_t[s][r][(t + tau) mod N]) = (1/N) DFT( sum_s G_s . conj(S_s) )[tau]
+// with G_s, S_s the forward transforms of the rows.  Both rows of each scan go through the DIF (same
+// digit-reversed order, so the product needs no reordering), the cross-spectrum accumulates in shared memory,
+// and one DIT pass sequence (a forward DFT of a digit-reversed row, natural-order output) gives every lag;
+// grad_w[r][k] = corr_r[o_k mod N].  Work per row: 2 n_scans + 1 transforms instead of n_scans * N * K MACs.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+azimuth_xspec_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St, const int32_t *__restrict__ o,
+                     int o_row_stride, int n_scans, int n_rng, int K, int N, RowPlan pl, float2 *__restrict__ grad_w) {
+    extern __shared__ float2 sm[];
+    const int pn = padded_len(N), sh = pl.pad_shift;
+    float2 *P = sm;
+    float2 *x = P + pn;
+    float2 *y = x + pn;
+    float2 *tw = y + pn;
+    const int r = blockIdx.x;
+    const float2 *tc, *tf;
+    build_twiddles(N, false, tw, &tc, &tf);
+    for (int n = threadIdx.x; n < pn; n += blockDim.x) P[n] = make_float2(0.f, 0.f);
+    for (int sc = 0; sc < n_scans; ++sc) {
+        const size_t row = ((size_t)sc * n_rng + r) * N;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            cp_async8(x + rpad(n, sh), g + row + n);
+            cp_async8(y + rpad(n, sh), St + row + n);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        row_dif(x, N, pl, tc, tf);
+        row_dif(y, N, pl, tc, tf);
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {      // P += X . conj(Y), same digit-reversed slot
+            const float2 a = x[rpad(n, sh)], b = y[rpad(n, sh)];
+            float2 &p = P[rpad(n, sh)];
+            p.x = fmaf(a.x, b.x, fmaf(a.y, b.y, p.x));
+            p.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, p.y));
+        }
+        __syncthreads();
+    }
+    row_dit(P, N, pl, tc, tf);
+    const float inv_n = (float)(1.0 / (double)N);
+    const int32_t *orow = o + (size_t)r * o_row_stride;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int tau = pmod(__ldg(orow + k), N);
+        grad_w[(size_t)r * K + k] = cscale(P[rpad(tau, sh)], inv_n);
+    }
 }
 
 constexpr size_t AF_SMEM_CAP = 200 * 1024;
@@ -155,7 +217,7 @@ int azimuth_fft_supported(int n_az) {
 
 template <int MAXT>
 cudaError_t launch_fft_rows(int g, int t, size_t sm, cudaStream_t s, bool overlap, const float2 *S, const float2 *H,
-                            int N, const RowPlan &pl, const Layout &lay, float2 *out) {
+                            int N, const RowPlan &pl, const Layout &lay, RowMap map, float2 *out) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g);
     cfg.blockDim = dim3(t);
@@ -166,7 +228,7 @@ cudaError_t launch_fft_rows(int g, int t, size_t sm, cudaStream_t s, bool overla
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = overlap ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, azimuth_fft_kernel<MAXT>, S, H, N, pl, lay, out);
+    return cudaLaunchKernelEx(&cfg, azimuth_fft_kernel<MAXT>, S, H, N, pl, lay, map, out);
 }
 
 namespace {
@@ -174,8 +236,8 @@ namespace {
 // Launches the compile-time-plan kernel when the run-time planner picks exactly its radices for n_az (so H,
 // made by the run-time plan, is in the same order); returns false to fall back to the run-time plan.
 template <int N, int... R>
-bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, bool ov, const float2 *S, const float2 *H,
-               float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
+bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, RowMap map, bool ov, const float2 *S,
+               const float2 *H, float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
     constexpr int T = 256;
     constexpr int rad[] = {R...};
     if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pl.npass != (int)sizeof...(R))
@@ -196,7 +258,7 @@ bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, bool o
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = ov ? 1 : 0;
-    *le = cudaLaunchKernelEx(&cfg, azimuth_fft_fixed_kernel<T, N, R...>, S, H, lay, out);
+    *le = cudaLaunchKernelEx(&cfg, azimuth_fft_fixed_kernel<T, N, R...>, S, H, lay, map, out);
     *st = check_launch("azimuth_fft");
     return true;
 }
@@ -204,7 +266,8 @@ bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, bool o
 }  // namespace
 
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
-                                bool overlap_predecessor) {
+                                bool overlap_predecessor, int h_rows, bool conj_h) {
+    const RowMap map{h_rows > 0 ? h_rows : n_rng, conj_h ? 1 : 0};
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
@@ -214,9 +277,9 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     {
         cudaError_t fle = cudaSuccess;
         rosar_status fst = ROSAR_OK;
-        if (try_fixed<3600, 16, 5, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<1800, 8, 5, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<360, 8, 5, 3, 3>(n_az, pl, n_rng, lay, ov, S, H, out, s, &fle, &fst)) {
+        if (try_fixed<3600, 16, 5, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<1800, 8, 5, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<360, 8, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst)) {
             if (fst == ROSAR_OK && fle != cudaSuccess)
                 return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(fle));
             return fst;
@@ -227,14 +290,34 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
                                       (const void *)azimuth_fft_kernel<512>, (const void *)azimuth_fft_kernel<1024>};
     rosar_status st = launch_rows(
         n_az, n_rng, lay.bytes,
-        [&](int g, int t, size_t sm) { le = launch_fft_rows<256>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
-        [&](int g, int t, size_t sm) { le = launch_fft_rows<384>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
-        [&](int g, int t, size_t sm) { le = launch_fft_rows<512>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
-        [&](int g, int t, size_t sm) { le = launch_fft_rows<1024>(g, t, sm, s, ov, S, H, n_az, pl, lay, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<256>(g, t, sm, s, ov, S, H, n_az, pl, lay, map, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<384>(g, t, sm, s, ov, S, H, n_az, pl, lay, map, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<512>(g, t, sm, s, ov, S, H, n_az, pl, lay, map, out); },
+        [&](int g, int t, size_t sm) { le = launch_fft_rows<1024>(g, t, sm, s, ov, S, H, n_az, pl, lay, map, out); },
         ks, done, "azimuth_fft");
     if (st == ROSAR_OK && le != cudaSuccess)
         return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(le));
     return st;
+}
+
+rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
+                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s) {
+    RowPlan pl;
+    if (!make_plan(n_az, &pl))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
+    const size_t bytes = sizeof(float2) * (3 * (size_t)padded_len(n_az) + 64 + coarse_len(n_az));
+    if (bytes > AF_SMEM_CAP)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: n_az=%d needs %zu bytes of shared memory", n_az, bytes);
+    static int done[4][kMaxDevices] = {};
+    static const void *const ks[4] = {(const void *)azimuth_xspec_kernel<256>, (const void *)azimuth_xspec_kernel<384>,
+                                      (const void *)azimuth_xspec_kernel<512>, (const void *)azimuth_xspec_kernel<1024>};
+    return launch_rows(
+        n_az, n_rng, bytes,
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<256><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<384><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<512><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<1024><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
+        ks, done, "weight_grad_fft");
 }
 
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,

@@ -401,6 +401,46 @@ rosar_status rosar_sparse_azimuth_adjoint(const rosar_c32 *g, const rosar_c32 *S
     return st;
 }
 
+rosar_status rosar_sparse_azimuth_fft_scans(const rosar_c32 *S, const rosar_c32 *H, int n_scans, int n_rng, int n_az,
+                                            int adjoint, rosar_c32 *out, void *stream) {
+    clear_error();
+    rosar_status st = check_stack("sparse_azimuth_fft_scans", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!S || !H || !out) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans: null pointer argument");
+    if (adjoint != 0 && adjoint != 1)
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans: adjoint must be 0 or 1");
+    if (misaligned(S, 8) || misaligned(H, 8) || misaligned(out, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az;
+    if (overlaps(out, b, S, b) || overlaps(out, b, H, sizeof(rosar_c32) * (size_t)n_rng * n_az))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans: out overlaps an input");
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth_fft_scans: n_az=%d is not 2^a 3^b 5^c <= 16384", n_az);
+    return launch_azimuth_fft(reinterpret_cast<const float2 *>(S), reinterpret_cast<const float2 *>(H), n_scans * n_rng,
+                              n_az, reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream), false, n_rng,
+                              adjoint == 1);
+}
+
+rosar_status rosar_azimuth_weight_grad_fft(const rosar_c32 *g, const rosar_c32 *S_t, const int32_t *o, int o_row_stride,
+                                           int n_scans, int n_rng, int n_az, int K, rosar_c32 *grad_w, void *stream) {
+    clear_error();
+    rosar_status st = check_stack("weight_grad_fft", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!g || !S_t || !o || !grad_w) return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft: null pointer argument");
+    if (K < 1 || (o_row_stride != 0 && o_row_stride < K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft: K=%d o_row_stride=%d", K, o_row_stride);
+    if ((long long)n_rng * K > kMaxElems || (long long)n_rng * o_row_stride > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: sizes too large");
+    if (misaligned(g, 8) || misaligned(S_t, 8) || misaligned(o, 4) || misaligned(grad_w, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az, gw = sizeof(rosar_c32) * (size_t)n_rng * K;
+    if (overlaps(grad_w, gw, g, b) || overlaps(grad_w, gw, S_t, b))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft: grad_w overlaps an input");
+    return launch_azimuth_weight_grad_fft(reinterpret_cast<const float2 *>(g), reinterpret_cast<const float2 *>(S_t), o,
+                                          o_row_stride, n_scans, n_rng, n_az, K, reinterpret_cast<float2 *>(grad_w),
+                                          static_cast<cudaStream_t>(stream));
+}
+
 rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *grad_S_t, const float *eps, int n_scans,
                               int n_rng, int n_az, float *grad_eps, rosar_c32 *grad_S, void *stream) {
     clear_error();

@@ -87,8 +87,13 @@ rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, in
 int azimuth_fft_supported(int n_az);
 // overlap_predecessor: launch with programmatic stream serialization (only when the preceding kernel in
 // the stream writes S and nothing else the kernel reads before its grid-dependency wait, i.e. H).
+// h_rows: row b of S uses row (b mod h_rows) of H (0 = n_rng: one plan row per S row); conj_h: filter with conj(H),
+// the adjoint of the filter.
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
-                                bool overlap_predecessor = false);
+                                bool overlap_predecessor = false, int h_rows = 0, bool conj_h = false);
+// grad_w[r][k] = sum_s sum_t g[s][r][t] conj(S_t[s][r][(t + o_k) mod n_az]) from the per-row cross-spectrum.
+rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
+                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s);
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
                                  float2 *H, cudaStream_t s);
 

@@ -301,6 +301,34 @@ def sparse_azimuth_adjoint(g, S_t, w, o, want_S=True, want_w=True, stream=None):
     return gS, gw
 
 
+def sparse_azimuth_fft_scans(S, H, adjoint=False, out=None, stream=None):
+    """rosar_sparse_azimuth_fft_scans: the frequency-domain filter of every scan of S [n_scans, n_rng, n_az]
+    with the shared plan H [n_rng, n_az]; adjoint=True filters with conj(H) (the filter's adjoint)."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    require(H, torch.complex64, "H", shape=(n_rng, n_az))
+    if out is None:
+        out = torch.empty_like(S)
+    require(out, torch.complex64, "out", shape=(n_scans, n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_fft_scans(ptr(S), ptr(H), n_scans, n_rng, n_az, 1 if adjoint else 0, ptr(out),
+                                             stream_handle(stream)))
+    return out
+
+
+def azimuth_weight_grad_fft(g, S_t, o, K, out=None, stream=None):
+    """rosar_azimuth_weight_grad_fft: grad_w [n_rng, K] from the per-row cross-spectrum of g and S_t."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(g, "g")
+    require(S_t, torch.complex64, "S_t", shape=(n_scans, n_rng, n_az))
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty((n_rng, K), dtype=torch.complex64, device=g.device)
+    require(out, torch.complex64, "grad_w", shape=(n_rng, K))
+    check(lib.rosar_azimuth_weight_grad_fft(ptr(g), ptr(S_t), ptr(o), stride, n_scans, n_rng, n_az, K, ptr(out),
+                                            stream_handle(stream)))
+    return out
+
+
 def phase_grad(S_t, grad_S_t, eps, want_eps=True, want_S=False, stream=None):
     """rosar_phase_grad: (grad_eps [n_scans, n_az] or None, grad_S or None)."""
     lib = _lib.load()

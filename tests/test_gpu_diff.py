@@ -101,13 +101,14 @@ def _oracle_loss(S, B, w, o, eps):
                      for s in range(S.shape[0])))
 
 
-def test_autograd_matches_fp64_finite_differences_on_crop(rosar):
+@pytest.mark.parametrize("method", ["gather", "fft"])
+def test_autograd_matches_fp64_finite_differences_on_crop(rosar, method):
     import torch
     S, B, w, o, eps = _crop_problem()
     tS = _cuda(torch, S).requires_grad_(True)
     te = _cuda(torch, eps).requires_grad_(True)
     tw = _cuda(torch, w).requires_grad_(True)
-    out = rosar.autograd.sparse_azimuth_phase(tS, te, tw, _cuda(torch, o))
+    out = rosar.autograd.sparse_azimuth_phase(tS, te, tw, _cuda(torch, o), method=method)
     loss = torch.sum(torch.abs(out - _cuda(torch, B)) ** 2)
     loss.backward()
     # FP64 oracle gradients
@@ -157,9 +158,10 @@ def test_range_compress_autograd(rosar):
     assert _rel(t.grad.cpu().numpy(), ref) < 1e-5
 
 
-def test_full_diff_workload_against_oracle(rosar):
+@pytest.mark.parametrize("method", ["gather", "fft"])
+def test_full_diff_workload_against_oracle(rosar, method):
     """16 indoor-geometry scans, shared w [256, 64], eps [16, 3600]: grad w and grad eps of
-    ||image - reference||^2 in the launch configuration the benchmark times, vs the FP64 oracle."""
+    ||image - reference||^2 in the launch configurations the benchmark times, vs the FP64 oracle."""
     import torch
     cfg = synth.INDOOR
     rng = np.random.default_rng(5)
@@ -171,7 +173,7 @@ def test_full_diff_workload_against_oracle(rosar):
     eps = (rng.standard_normal((n_scans, cfg.n_az)) * 0.3).astype(np.float32)
     tw = _cuda(torch, w).requires_grad_(True)
     te = _cuda(torch, eps).requires_grad_(True)
-    out = rosar.autograd.sparse_azimuth_phase(_cuda(torch, S), te, tw, _cuda(torch, o))
+    out = rosar.autograd.sparse_azimuth_phase(_cuda(torch, S), te, tw, _cuda(torch, o), method=method)
     torch.sum(torch.abs(out - _cuda(torch, Bref)) ** 2).backward()
     gw = tw.grad.cpu().numpy()
     ge = te.grad.cpu().numpy()
@@ -183,3 +185,31 @@ def test_full_diff_workload_against_oracle(rosar):
         if s in (0, 15):
             assert _rel(ge[s], O.phase_error_grad(St, O.sparse_azimuth_adjoint_S(gr, w, o))) < TOL_GRAD
     assert _rel(gw, ref_w) < TOL_GRAD
+
+
+@pytest.mark.parametrize("n_az,per_row", [(48, False), (1000, True), (3600, False), (7200, True)])
+def test_frequency_domain_adjoints_match_oracle(rosar, n_az, per_row):
+    """Stacked FFT filter (plan shared by the scans), its adjoint (conj of the plan) and the cross-spectrum
+    weight gradient against the oracle's filter and adjoints; shared and per-row offsets, wrapping offsets."""
+    import torch
+    rng = np.random.default_rng(n_az)
+    n_scans, n_rng, K = 3, 5, 12
+    M = min(n_az, 600)
+    if per_row:
+        o = np.stack([np.sort(rng.choice(M, K, replace=False)) - M // 2 for _ in range(n_rng)]).astype(np.int32)
+        o[1, 0] -= 3 * n_az
+    else:
+        o = (np.sort(rng.choice(M, K, replace=False)) - M // 2).astype(np.int32)
+    S, g = _c(rng, n_scans, n_rng, n_az), _c(rng, n_scans, n_rng, n_az)
+    w = _c(rng, n_rng, K)
+    tw, to = _cuda(torch, w), _cuda(torch, o)
+    H = rosar.azimuth_plan(tw, to, n_az)
+    out = rosar.sparse_azimuth_fft_scans(_cuda(torch, S), H).cpu().numpy()
+    adj = rosar.sparse_azimuth_fft_scans(_cuda(torch, g), H, adjoint=True).cpu().numpy()
+    gw = rosar.azimuth_weight_grad_fft(_cuda(torch, g), _cuda(torch, S), to, K).cpu().numpy()
+    ref_w = np.zeros((n_rng, K), np.complex128)
+    for s in range(n_scans):
+        assert _rel(out[s], O.sparse_azimuth(S[s], w, o)) < 1e-5
+        assert _rel(adj[s], O.sparse_azimuth_adjoint_S(g[s], w, o)) < 1e-5
+        ref_w += O.sparse_azimuth_adjoint_w(g[s], S[s], o)
+    assert _rel(gw, ref_w) < 1e-5
