@@ -29,6 +29,8 @@
 
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "rosar_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -235,6 +237,293 @@ td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, cons
     }
 }
 
+// ------------------------------------------------------------------ tensor-core form (tcgen05) --
+// The same implicit GEMM on the 5th-generation tensor cores.  A complex product a*b is the real product of
+// [a.re a.im] (two K entries of A) with [[b.re, b.im], [-b.im, b.re]] (a 2 x 2 block of B: K = (sample, re/im),
+// N = (row, re/im)), so D[theta][(row, re/im)] accumulates the complex sum in fp32 in tensor memory.  bf16
+// operands hold 8 significant bits; each operand is split as x = hi + lo (bf16 each, x - hi exact to 2^-16 of
+// x) and the product taken as hi*hi + hi*lo + lo*hi (three MMAs per K step), which keeps products within a few
+// 10^-5 of fp32 (the dropped lo*lo term is 2^-16 smaller).  Per stage (one tap, 16 samples) the threads write
+// the A tiles (128 pulses x 32 reals, split) and the B tiles (128 (row, re/im) x 32 reals: coefficient x window
+// x fast-time phasor, split) into shared memory in the canonical no-swizzle K-major layout (8 x 16-byte core
+// matrices; K-adjacent ones 128 B apart, 8-row groups 512 B apart), double-buffered; one thread issues the 2 K
+// steps x 3 MMAs (M = 128, N = 128, K = 16) and commits them to the stage buffer's mbarrier, which the
+// producers wait on before refilling that buffer.  Taps split across a cluster as in td_tile_kernel.
+namespace tcg {
+constexpr int THREADS = 256;
+constexpr int BT = 128;                      // azimuth pixels per CTA = MMA M
+constexpr int BR = 64;                       // rows per CTA
+constexpr int NN = 2 * BR;                   // MMA N
+constexpr int MC = 16;                       // samples per stage
+constexpr int KR = 2 * MC;                   // K entries (reals) per stage
+constexpr int SBO = (KR / 8) * 128;          // byte stride of 8-row groups
+constexpr int LBO = 128;                     // byte stride of K-adjacent core matrices
+constexpr int TILE = BT * KR * 2;            // bytes of one operand tile (A: 128 x 32 bf16; B: NN = 128 rows)
+constexpr int STAGE = 4 * TILE;              // A hi, A lo, B hi, B lo
+constexpr int SMEM = 2 * STAGE + 3 * BR * 16 + 64;
+constexpr int TMEM_COLS = 2 * NN;             // period accumulator X, running sum Y
+constexpr int PERIOD = 128;                  // stages per period: 768 MMA steps accumulate in X before X is added into Y
+constexpr long long SPIN_LIMIT = 1LL << 26;
+static_assert(NN == BT, "one tile size serves both operands");
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int off(int row, int kk) {
+    return (row >> 3) * SBO + (kk >> 3) * LBO + (row & 7) * 16 + (kk & 7) * 2;
+}
+__device__ __forceinline__ uint64_t desc(uint32_t a) {
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+// D fp32, A and B bf16, both K-major, N = NN, M = BT
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(BT >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+__device__ __forceinline__ void ld16(uint32_t ta, float *v) {
+    uint32_t rr[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                   "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                   "=r"(rr[15])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rr[j]);
+}
+__device__ __forceinline__ void st16(uint32_t ta, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(ta), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                   "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                   "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                   "r"(__float_as_uint(v[15]))
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+// bounded wait for the completion of phase `parity` of an mbarrier; false after SPIN_LIMIT polls
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity) {
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(saddr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// hi and lo bf16 pairs of (x, y): hi = RN(x, y), lo = RN(x - hi.x, y - hi.y)
+__device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+}  // namespace tcg
+
+template <bool BPA>
+__global__ void __launch_bounds__(tcg::THREADS, 2)
+td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
+             const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
+    using namespace tcg;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
+    float4 *tab = reinterpret_cast<float4 *>(smem + 2 * STAGE);  // [3][BR]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 3 * BR * 16);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int th0 = blockIdx.x * BT, r0 = blockIdx.y * BR;
+    const int n_az = p.n_az, L = p.L;
+    const int chunks = L / MC;
+    const int k_lo = blockIdx.z * k_per;
+    const int nk = max(0, min(K, k_lo + k_per) - k_lo);
+    const int stages = nk * chunks;
+    const bool wide = n_az >= BT;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&bars[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&bars[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    auto tap_off = [&](int kk) -> int {
+        const int k = k_lo + kk;
+        return BPA ? k - K / 2 : pmod(__ldg(o + k), n_az);
+    };
+    auto build_tab = [&](int kk) {           // warps 0-1: one row per thread
+        const int j = tid;
+        const int r = r0 + j;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < p.n_rng) {
+            t = tap_entry<BPA>(p, r, tap_off(kk));
+            if (!BPA) {
+                const float2 c = __ldg(w + (size_t)r * K + k_lo + kk);
+                t.x = c.x;
+                t.y = c.y;
+            }
+        }
+        tab[(kk % 3) * BR + j] = t;
+    };
+    if (warp < 2 && stages > 0) {
+        build_tab(0);
+        if (nk > 1) build_tab(1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // X (columns 0..NN) takes the MMAs of one period; at the period's end every thread folds its lanes and columns
+    // of X into Y (columns NN..2NN) with round-to-nearest fp32 adds (tensor-core accumulation keeps a small
+    // one-sided error per step; over a period of 768 steps it stays near 1e-5 relative)
+    const int q = warp & 3, h = warp >> 2;
+    const uint32_t x_ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
+    const uint32_t y_ta = x_ta + (uint32_t)NN;
+    bool have_y = false;
+    auto fold = [&]() {                       // Y (+)= X, this warp's 32 lanes x 64 columns
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            float xv[16], yv[16];
+            ld16(x_ta + 16 * c, xv);
+            if (have_y) {
+                ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) xv[j] += yv[j];
+            }
+            st16(y_ta + 16 * c, xv);
+        }
+        have_y = true;
+    };
+
+    bool ok = true;
+    for (int s = 0; s < stages && ok; ++s) {
+        const int b = s & 1;
+        uint8_t *st = stage_base + b * STAGE;
+        if (s >= 2) ok = wait_bar(&bars[b], (uint32_t)(((s - 2) >> 1) & 1));   // MMAs of stage s-2 done
+        if (!ok) break;
+        const int kk = s / chunks, m0 = (s - kk * chunks) * MC;
+        if (warp < 2 && s % chunks == 0 && kk + 2 < nk) build_tab(kk + 2);
+        // A: 128 pulses x 16 samples, split; lanes cover one core matrix per store
+        const int base = pmod(th0 + tap_off(kk), n_az);
+#pragma unroll
+        for (int it = 0; it < BT * MC / THREADS; ++it) {
+            const int e = tid + THREADS * it;
+            const int m = ((e >> 5) & 3) * 4 + (e & 3), t = (e >> 7) * 8 + ((e >> 2) & 7);
+            int row = base + t;
+            if (wide) row = row >= n_az ? row - n_az : row;
+            else row %= n_az;
+            const float2 a = __ldg(X + (size_t)row * L + m0 + m);
+            uint32_t hi, lo;
+            split2(a.x, a.y, hi, lo);
+            *reinterpret_cast<uint32_t *>(st + off(t, 2 * m)) = hi;
+            *reinterpret_cast<uint32_t *>(st + TILE + off(t, 2 * m)) = lo;
+        }
+        // B: 64 rows x 16 samples of coefficient x window x phasor, as rows (r, re) = [b.re, -b.im] and
+        // (r, im) = [b.im, b.re] per sample
+        const float4 *tb = tab + (kk % 3) * BR;
+#pragma unroll
+        for (int it = 0; it < BR * MC / THREADS; ++it) {
+            const int e = tid + THREADS * it;
+            const int m = ((e >> 5) & 3) * 4 + (e & 3);
+            const int r = (e >> 7) * 8 + ((e >> 4) & 1) * 4 + ((e >> 2) & 3);
+            const float wm = win ? __ldg(win + m0 + m) : 1.f;
+            const float2 v = phasor_term(tb[r], wm, (float)(m0 + m) - p.m_ref);
+            uint32_t hi, lo;
+            split2(v.x, -v.y, hi, lo);
+            *reinterpret_cast<uint32_t *>(st + 2 * TILE + off(2 * r, 2 * m)) = hi;
+            *reinterpret_cast<uint32_t *>(st + 3 * TILE + off(2 * r, 2 * m)) = lo;
+            split2(v.y, v.x, hi, lo);
+            *reinterpret_cast<uint32_t *>(st + 2 * TILE + off(2 * r + 1, 2 * m)) = hi;
+            *reinterpret_cast<uint32_t *>(st + 3 * TILE + off(2 * r + 1, 2 * m)) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = saddr(st), a_lo = a_hi + TILE, b_hi = a_hi + 2 * TILE, b_lo = a_hi + 3 * TILE;
+#pragma unroll
+            for (int ks = 0; ks < KR / 16; ++ks) {
+                const uint32_t ko = ks * 2 * LBO;                     // 16 K entries = two core-matrix columns
+                mma(tmem, desc(a_hi + ko), desc(b_hi + ko), (s % PERIOD != 0 || ks > 0) ? 1u : 0u);
+                mma(tmem, desc(a_hi + ko), desc(b_lo + ko), 1u);
+                mma(tmem, desc(a_lo + ko), desc(b_hi + ko), 1u);
+            }
+            commit(&bars[b]);
+        }
+        if ((s + 1) % PERIOD == 0 && s + 1 < stages) {   // end of a period: wait for its MMAs, fold X into Y
+            ok = wait_bar(&bars[b], (uint32_t)((s >> 1) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            fold();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();                      // X is free for the next period's first MMA
+        }
+    }
+    if (ok && stages > 0) ok = wait_bar(&bars[(stages - 1) & 1], (uint32_t)(((stages - 1) >> 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // accumulator -> registers: warp w reads TMEM lanes 32 (w % 4).. (pixels) and columns 64 (w / 4)..
+    const int th = 32 * q + lane;
+    float v[64];
+    if (ok && stages > 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            ld16(x_ta + 16 * c, v + 16 * c);
+            if (have_y) {
+                float yv[16];
+                ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[16 * c + j] += yv[j];
+            }
+        }
+    } else {
+        const float f = ok ? 0.f : __int_as_float(0x7fc00000);   // no taps: zero; a wait that gave up: NaN
+#pragma unroll
+        for (int j = 0; j < 64; ++j) v[j] = f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+
+    const int G = gridDim.z;
+    if (G > 1) {                              // partial tiles parked in the stage buffers, rank 0 adds in rank order
+        float *red = reinterpret_cast<float *>(smem);            // [128 columns][128 pixels] = 64 KB
+        cg::cluster_group cluster = cg::this_cluster();
+#pragma unroll
+        for (int j = 0; j < 64; ++j) red[(64 * h + j) * BT + th] = v[j];
+        cluster.sync();
+        if (cluster.block_rank() == 0) {
+            for (int rk = 1; rk < G; ++rk) {
+                const float *rem = cluster.map_shared_rank(red, rk);
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] += rem[(64 * h + j) * BT + th];
+            }
+        }
+        cluster.sync();
+        if (cluster.block_rank() != 0) return;
+    }
+    const int tcol = th0 + th;
+    if (tcol < n_az) {
+#pragma unroll
+        for (int j = 0; j < 64; j += 2) {
+            const int r = r0 + (64 * h + j) / 2;
+            if (r < p.n_rng) out[(size_t)r * n_az + tcol] = make_float2(v[j], v[j + 1]);
+        }
+    }
+}
+
 // Per-row offsets: one CTA per (row, block of TR_BT pixels), two pixels per thread.  Samples are taken in
 // chunks of TR_MC: the row's B chunk (all taps x TR_MC samples; one sincospif each) is generated into
 // shared memory, then every thread sweeps taps and samples, reading its pulses' samples as float4 pairs.
@@ -372,6 +661,74 @@ rosar_status launch_tiles(const float2 *raw, const float *win, const float2 *w, 
     return check_launch(BPA ? "bpa_time" : "sas_time");
 }
 
+// Cluster size for the tensor-core kernel, as pick_cluster (its own occupancy: dynamic shared memory, 256 threads).
+template <bool BPA>
+int pick_cluster_tc(int tiles, int K) {
+    static int cached_dev = -1, cached_tiles = -1, cached_K = -1, cached_G = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev == cached_dev && tiles == cached_tiles && K == cached_K) return cached_G;
+    int best_G = 1;
+    double best = -1.0;
+    for (int G = 1; G <= TD_MAX_CLUSTER; ++G) {
+        if (G > 1 && (K < 4 * G)) break;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(1, 1, G);
+        cfg.blockDim = dim3(tcg::THREADS);
+        cfg.dynamicSmemBytes = tcg::SMEM;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = G;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, td_tc_kernel<BPA>, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const double waves = (double)tiles / clusters;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best + 1e-3) {
+            best = eff;
+            best_G = G;
+        }
+    }
+    cached_dev = dev;
+    cached_tiles = tiles;
+    cached_K = K;
+    cached_G = best_G;
+    return best_G;
+}
+
+template <bool BPA>
+rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
+                       float2 *out, cudaStream_t s) {
+    static int done[kMaxDevices] = {};
+    rosar_status st = ensure_smem((const void *)td_tc_kernel<BPA>, tcg::SMEM, done, BPA ? "bpa_time" : "sas_time");
+    if (st != ROSAR_OK) return st;
+    const int gx = (p.n_az + tcg::BT - 1) / tcg::BT, gy = (p.n_rng + tcg::BR - 1) / tcg::BR;
+    const int G = pick_cluster_tc<BPA>(gx * gy, K);
+    const int k_per = (K + G - 1) / G;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(gx, gy, G);
+    cfg.blockDim = dim3(tcg::THREADS);
+    cfg.dynamicSmemBytes = tcg::SMEM;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = G;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tc_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
+    if (e != cudaSuccess)
+        return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", BPA ? "bpa_time" : "sas_time", cudaGetErrorString(e));
+    return check_launch(BPA ? "bpa_time" : "sas_time");
+}
+
 }  // namespace
 
 int time_domain_sample_multiple() { return TD_MC; }
@@ -382,7 +739,7 @@ rosar_status launch_time_domain(const float2 *raw, const float *win, const float
     if (bpa || o_row_stride == 0) {
         if ((p.n_rng + TD_BR - 1) / TD_BR > 65535)
             return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
-        return bpa ? launch_tiles<true>(raw, win, w, o, p, K, out, s) : launch_tiles<false>(raw, win, w, o, p, K, out, s);
+        return bpa ? launch_tc<true>(raw, win, w, o, p, K, out, s) : launch_tc<false>(raw, win, w, o, p, K, out, s);
     }
     if (p.n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
     dim3 grid((p.n_az + TR_BT - 1) / TR_BT, p.n_rng);
