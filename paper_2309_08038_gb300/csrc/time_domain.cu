@@ -260,7 +260,8 @@ constexpr int SBO = (KR / 8) * 128;          // byte stride of 8-row groups
 constexpr int LBO = 128;                     // byte stride of K-adjacent core matrices
 constexpr int TILE = BT * KR * 2;            // bytes of one operand tile (A: 128 x 32 bf16; B: NN = 128 rows)
 constexpr int STAGE = 4 * TILE;              // A hi, A lo, B hi, B lo
-constexpr int SMEM = 2 * STAGE + 3 * BR * 16 + 64;
+constexpr int AF = BT * MC * 8;              // fp32 A staging of one stage (cp.async target): 16 KB
+constexpr int SMEM = 2 * STAGE + 2 * AF + 3 * BR * 16 + 64;
 constexpr int TMEM_COLS = 2 * NN;             // period accumulator X, running sum Y
 constexpr int PERIOD = 128;                  // stages per period: 768 MMA steps accumulate in X before X is added into Y
 constexpr long long SPIN_LIMIT = 1LL << 26;
@@ -335,8 +336,9 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     using namespace tcg;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
-    float4 *tab = reinterpret_cast<float4 *>(smem + 2 * STAGE);  // [3][BR]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 3 * BR * 16);
+    float2 *af = reinterpret_cast<float2 *>(smem + 2 * STAGE);   // [2][BT][MC] raw samples, one stage ahead
+    float4 *tab = reinterpret_cast<float4 *>(smem + 2 * STAGE + 2 * AF);  // [3][BR]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 2 * AF + 3 * BR * 16);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -407,6 +409,33 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         have_y = true;
     };
 
+    // A copies of one stage: thread copies (and later converts) 4 pairs of samples: pair e = tid + THREADS*it,
+    // row t = 8 (e >> 4 ... ) + ((e >> 1) & 7), samples m = 4 ((e >> 4) & 3) + 2 (e & 1) .. +1; lanes 0-15 cover one
+    // core matrix (8 rows x 16 B) of the bf16 tiles, so the 8-byte stores are conflict-free
+    auto a_pair = [&](int it, int &t, int &m) {
+        const int e = tid + THREADS * it;
+        m = ((e >> 4) & 3) * 4 + (e & 1) * 2;
+        t = (e >> 6) * 8 + ((e >> 1) & 7);
+    };
+    auto prefetch_A = [&](int s2) {
+        const int kk2 = s2 / chunks, m02 = (s2 - kk2 * chunks) * MC;
+        const int base2 = pmod(th0 + tap_off(kk2), n_az);
+        float2 *dst = af + (s2 & 1) * (BT * MC);
+#pragma unroll
+        for (int it = 0; it < BT * MC / 2 / THREADS; ++it) {
+            int t, m;
+            a_pair(it, t, m);
+            int row = base2 + t;
+            if (wide) row = row >= n_az ? row - n_az : row;
+            else row %= n_az;
+            const unsigned d = saddr(dst + t * MC + m);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(X + (size_t)row * L + m02 + m)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (stages > 0) prefetch_A(0);
+
     bool ok = true;
     for (int s = 0; s < stages && ok; ++s) {
         const int b = s & 1;
@@ -414,39 +443,57 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         if (s >= 2) ok = wait_bar(&bars[b], (uint32_t)(((s - 2) >> 1) & 1));   // MMAs of stage s-2 done
         if (!ok) break;
         const int kk = s / chunks, m0 = (s - kk * chunks) * MC;
-        if (warp < 2 && s % chunks == 0 && kk + 2 < nk) build_tab(kk + 2);
-        // A: 128 pulses x 16 samples, split; lanes cover one core matrix per store
-        const int base = pmod(th0 + tap_off(kk), n_az);
-#pragma unroll
-        for (int it = 0; it < BT * MC / THREADS; ++it) {
-            const int e = tid + THREADS * it;
-            const int m = ((e >> 5) & 3) * 4 + (e & 3), t = (e >> 7) * 8 + ((e >> 2) & 7);
-            int row = base + t;
-            if (wide) row = row >= n_az ? row - n_az : row;
-            else row %= n_az;
-            const float2 a = __ldg(X + (size_t)row * L + m0 + m);
-            uint32_t hi, lo;
-            split2(a.x, a.y, hi, lo);
-            *reinterpret_cast<uint32_t *>(st + off(t, 2 * m)) = hi;
-            *reinterpret_cast<uint32_t *>(st + TILE + off(t, 2 * m)) = lo;
+        if (s + 1 < stages) {
+            prefetch_A(s + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");           // this thread's copies of stage s
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        // B: 64 rows x 16 samples of coefficient x window x phasor, as rows (r, re) = [b.re, -b.im] and
-        // (r, im) = [b.im, b.re] per sample
-        const float4 *tb = tab + (kk % 3) * BR;
+        if (warp < 2 && s % chunks == 0 && kk + 2 < nk) build_tab(kk + 2);
+        // A: the thread's own 4 pairs of samples, split into the hi and lo tiles
+        const float2 *src = af + b * (BT * MC);
 #pragma unroll
-        for (int it = 0; it < BR * MC / THREADS; ++it) {
-            const int e = tid + THREADS * it;
-            const int m = ((e >> 5) & 3) * 4 + (e & 3);
-            const int r = (e >> 7) * 8 + ((e >> 4) & 1) * 4 + ((e >> 2) & 3);
-            const float wm = win ? __ldg(win + m0 + m) : 1.f;
-            const float2 v = phasor_term(tb[r], wm, (float)(m0 + m) - p.m_ref);
-            uint32_t hi, lo;
-            split2(v.x, -v.y, hi, lo);
-            *reinterpret_cast<uint32_t *>(st + 2 * TILE + off(2 * r, 2 * m)) = hi;
-            *reinterpret_cast<uint32_t *>(st + 3 * TILE + off(2 * r, 2 * m)) = lo;
-            split2(v.y, v.x, hi, lo);
-            *reinterpret_cast<uint32_t *>(st + 2 * TILE + off(2 * r + 1, 2 * m)) = hi;
-            *reinterpret_cast<uint32_t *>(st + 3 * TILE + off(2 * r + 1, 2 * m)) = lo;
+        for (int it = 0; it < BT * MC / 2 / THREADS; ++it) {
+            int t, m;
+            a_pair(it, t, m);
+            const float4 a = *reinterpret_cast<const float4 *>(src + t * MC + m);
+            uint2 hi, lo;
+            split2(a.x, a.y, hi.x, lo.x);
+            split2(a.z, a.w, hi.y, lo.y);
+            *reinterpret_cast<uint2 *>(st + off(t, 2 * m)) = hi;
+            *reinterpret_cast<uint2 *>(st + TILE + off(t, 2 * m)) = lo;
+        }
+        // B: thread = (row r = 8 warp + (lane & 7), 4 samples 4 (lane >> 3) ..): coefficient x window x phasor by a
+        // recurrence over the 4 samples, written as rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes
+        // with r & 4 write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
+        {
+            const int r = 8 * warp + (lane & 7), c = lane >> 3;
+            const float4 t4 = tab[(kk % 3) * BR + r];
+            const int mb = m0 + 4 * c;
+            const float2 e0 = phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref);
+            float sn, cs;
+            sincospif(t4.z, &sn, &cs);
+            const float2 step = make_float2(cs, -sn);                        // exp(-j pi phi), one sample
+            float2 e = e0;
+            uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float wm = win ? __ldg(win + mb + i) : 1.f;
+                const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
+                split2(v.x, -v.y, re_hi[i], re_lo[i]);
+                split2(v.y, v.x, im_hi[i], im_lo[i]);
+                e = cmul(e, step);
+            }
+            const bool swap = (r & 4) != 0;
+            const int o_re = off(2 * r, 8 * c), o_im = off(2 * r + 1, 8 * c);
+            const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+            const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+            const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+            const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+            *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_im : o_re)) = swap ? ih : rh;
+            *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_im : o_re)) = swap ? il : rl;
+            *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_re : o_im)) = swap ? rh : ih;
+            *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_re : o_im)) = swap ? rl : il;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
