@@ -17,13 +17,13 @@
 //
 // With offsets shared by all rows the filter is an implicit complex GEMM over the index (k, m):
 //   out[theta][r] = sum_(k,m) A[theta][(k,m)] * B[(k,m)][r],  A = raw[theta + o_k][m],  B = c*win*phasor,
-// tiled as 128 azimuth pixels x 32 rows per CTA.  Each stage (one tap, 16 samples) stages the A tile
-// (128 pulses x 16 samples, from L2) and generates the B tile (32 rows x 16 samples, one sincospif
-// each) in shared memory, double-buffered; each thread accumulates a 4 x 4 register tile (FP32 FMA).
-// Per-row offsets (Algorithm 2 with a support per range bin) use a row kernel: one row per CTA, the
-// row's phasors staged in shared memory by sample chunk, pulses read through L1/L2.
+// run on the tensor cores (td_tc_kernel below): 128 azimuth pixels x 64 rows per CTA, per stage (one tap,
+// 16 samples) an A tile of raw samples and a B tile of generated coefficients in shared memory, tcgen05 MMAs
+// into a tensor-memory accumulator.  Per-row offsets (Algorithm 2 with a support per range bin) use a row
+// kernel on the CUDA cores: one row per CTA, the row's phasors staged in shared memory by sample chunk,
+// pulses read through L1/L2.
 //
-// Compute-bound on FP32 FMA: 8 flops per (pixel, tap, sample).
+// 8 flops per (pixel, tap, sample).
 
 #include <cooperative_groups.h>
 
@@ -38,21 +38,8 @@ namespace cg = cooperative_groups;
 namespace rosar {
 namespace {
 
-constexpr int TD_THREADS = 128;
-constexpr int TD_BT = 128;   // azimuth pixels per CTA
-constexpr int TD_BR = 32;    // range rows per CTA (= warp size: one table entry per lane of warp 0)
 constexpr int TD_MC = 16;    // fast-time samples per stage
-constexpr int TD_AS = TD_MC + 1;                  // A row stride in elements (odd: conflict-free column reads)
-constexpr int TD_TQ = TD_BT / 32;                 // azimuth pixels per thread (4): lane + 32 q
-constexpr int TD_TI = TD_BR / (TD_THREADS / 32);  // rows per thread (8): 8 * warp + i
 constexpr int TD_MAX_CLUSTER = 8;
-
-__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // (c.re, c.im, phi_hi, phi_lo) of tap offset o in row r; c is only filled for BPA.
 template <bool BPA>
@@ -92,151 +79,6 @@ __device__ __forceinline__ float2 phasor_term(float4 t, float wm, float x) {
     return cmul(c, make_float2(cs, -sn));
 }
 
-// One CTA = TD_BT pixels x TD_BR rows x the taps [k_lo, k_hi) of its cluster rank.  With a cluster of G > 1
-// CTAs along z the taps are split in G contiguous ranges and rank 0 adds the other ranks' partial tiles,
-// read from their shared memory, in rank order (deterministic).
-template <bool BPA>
-__global__ void __launch_bounds__(TD_THREADS, 4)
-td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
-               const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
-    __shared__ __align__(16) float2 As[2][TD_BT * TD_AS];
-    __shared__ __align__(16) float2 Bs[2][TD_MC][TD_BR];
-    __shared__ float4 tab[3][TD_BR];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int th0 = blockIdx.x * TD_BT, r0 = blockIdx.y * TD_BR;
-    const int n_az = p.n_az, L = p.L;
-    const int chunks = L / TD_MC;
-    const int k_lo = blockIdx.z * k_per;
-    const int nk = max(0, min(K, k_lo + k_per) - k_lo);
-    const int stages = nk * chunks;
-    const bool wide = n_az >= TD_BT;            // one conditional subtraction wraps a tile row index
-
-    auto tap_off = [&](int kk) -> int {
-        const int k = k_lo + kk;
-        return BPA ? k - K / 2 : pmod(__ldg(o + k), n_az);
-    };
-    auto build_tab = [&](int kk) {              // warp 0: one row per lane
-        const int r = r0 + lane;
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < p.n_rng) {
-            t = tap_entry<BPA>(p, r, tap_off(kk));
-            if (!BPA) {
-                const float2 c = __ldg(w + (size_t)r * K + k_lo + kk);
-                t.x = c.x;
-                t.y = c.y;
-            }
-        }
-        tab[kk % 3][lane] = t;
-    };
-    auto load_A = [&](int s, int buf) {         // 128 pulses x 16 samples by 8-byte cp.async, transposed rows
-        const int kk = s / chunks, m0 = (s - kk * chunks) * TD_MC;
-        const int base = pmod(th0 + tap_off(kk), n_az);
-        const int m = tid & (TD_MC - 1);
-#pragma unroll
-        for (int j = 0; j < TD_BT * TD_MC / TD_THREADS; ++j) {
-            const int t = (tid >> 4) + j * (TD_THREADS / TD_MC);
-            int row = base + t;
-            if (wide) row = row >= n_az ? row - n_az : row;
-            else row %= n_az;
-            cp_async8(&As[buf][t * TD_AS + m], X + (size_t)row * L + m0 + m);
-        }
-        cp_async_commit();
-    };
-    auto gen_B = [&](int s, int buf) {
-        const int kk = s / chunks, m0 = (s - kk * chunks) * TD_MC;
-#pragma unroll
-        for (int q = 0; q < TD_BR * TD_MC / TD_THREADS; ++q) {
-            const int v = tid + TD_THREADS * q;
-            const int j = v & (TD_BR - 1), m = v >> 5;
-            const float wm = win ? __ldg(win + m0 + m) : 1.f;
-            Bs[buf][m][j] = phasor_term(tab[kk % 3][j], wm, (float)(m0 + m) - p.m_ref);
-        }
-    };
-
-    float2 acc[TD_TQ][TD_TI];
-#pragma unroll
-    for (int q = 0; q < TD_TQ; ++q)
-#pragma unroll
-        for (int i = 0; i < TD_TI; ++i) acc[q][i] = make_float2(0.f, 0.f);
-
-    if (stages > 0) {
-        if (warp == 0) {
-            build_tab(0);
-            if (nk > 1) build_tab(1);
-        }
-        load_A(0, 0);
-        __syncthreads();
-        gen_B(0, 0);
-        cp_async_wait_all();
-        __syncthreads();
-    }
-    for (int s = 0; s < stages; ++s) {
-        const int buf = s & 1;
-        const bool more = s + 1 < stages;
-        if (more) load_A(s + 1, buf ^ 1);
-        if (warp == 0 && s % chunks == 0) {
-            const int kk = s / chunks + 2;
-            if (kk < nk) build_tab(kk);
-        }
-        const float2 *arow = &As[buf][lane * TD_AS];
-#pragma unroll 4                                 // full unrolling overflows the instruction cache
-        for (int m = 0; m < TD_MC; ++m) {
-            float2 a[TD_TQ], b[TD_TI];
-#pragma unroll
-            for (int q = 0; q < TD_TQ; ++q) a[q] = arow[32 * q * TD_AS + m];
-            const float4 *bp = reinterpret_cast<const float4 *>(&Bs[buf][m][TD_TI * warp]);
-#pragma unroll
-            for (int i = 0; i < TD_TI / 2; ++i) {
-                const float4 v = bp[i];
-                b[2 * i] = make_float2(v.x, v.y);
-                b[2 * i + 1] = make_float2(v.z, v.w);
-            }
-#pragma unroll
-            for (int q = 0; q < TD_TQ; ++q)
-#pragma unroll
-                for (int i = 0; i < TD_TI; ++i) cmac(acc[q][i], a[q], b[i]);
-        }
-        if (more) gen_B(s + 1, buf ^ 1);
-        cp_async_wait_all();
-        __syncthreads();
-    }
-
-    // cluster split: every rank parks its partial tile in its own shared memory, rank 0 adds them in order
-    const int G = gridDim.z;
-    if (G > 1) {
-        float2 *red = &As[0][0];                // 32 * 128 float2 = 32 KB <= sizeof(As)
-        cg::cluster_group cluster = cg::this_cluster();
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < TD_TQ; ++q)
-#pragma unroll
-            for (int i = 0; i < TD_TI; ++i) red[(q * TD_TI + i) * TD_THREADS + tid] = acc[q][i];
-        cluster.sync();
-        if (cluster.block_rank() == 0) {
-            for (int rk = 1; rk < G; ++rk) {
-                const float2 *rem = cluster.map_shared_rank(red, rk);
-#pragma unroll
-                for (int q = 0; q < TD_TQ; ++q)
-#pragma unroll
-                    for (int i = 0; i < TD_TI; ++i) acc[q][i] = cadd(acc[q][i], rem[(q * TD_TI + i) * TD_THREADS + tid]);
-            }
-        }
-        cluster.sync();                         // the other ranks keep their shared memory until rank 0 is done
-        if (cluster.block_rank() != 0) return;
-    }
-#pragma unroll
-    for (int i = 0; i < TD_TI; ++i) {
-        const int r = r0 + TD_TI * warp + i;
-        if (r >= p.n_rng) continue;
-#pragma unroll
-        for (int q = 0; q < TD_TQ; ++q) {
-            const int th = th0 + lane + 32 * q;
-            if (th < n_az) out[(size_t)r * n_az + th] = acc[q][i];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ tensor-core form (tcgen05) --
 // The same implicit GEMM on the 5th-generation tensor cores.  A complex product a*b is the real product of
 // [a.re a.im] (two K entries of A) with [[b.re, b.im], [-b.im, b.re]] (a 2 x 2 block of B: K = (sample, re/im),
@@ -250,7 +92,8 @@ td_tile_kernel(const float2 *__restrict__ X, const float *__restrict__ win, cons
 // steps x 3 MMAs (M = 128, N = 128, K = 16) and commits them to the stage buffer's mbarrier, which the
 // producers wait on before refilling that buffer.  Taps split across a cluster as in td_tile_kernel.
 namespace tcg {
-constexpr int THREADS = 256;
+constexpr int PRODUCERS = 256;               // warps 0-7 stage the operands and read the accumulator
+constexpr int THREADS = PRODUCERS + 32;      // warp 8 issues the MMAs
 constexpr int BT = 128;                      // azimuth pixels per CTA = MMA M
 constexpr int BR = 64;                       // rows per CTA
 constexpr int NN = 2 * BR;                   // MMA N
@@ -260,7 +103,8 @@ constexpr int SBO = (KR / 8) * 128;          // byte stride of 8-row groups
 constexpr int LBO = 128;                     // byte stride of K-adjacent core matrices
 constexpr int TILE = BT * KR * 2;            // bytes of one operand tile (A: 128 x 32 bf16; B: NN = 128 rows)
 constexpr int STAGE = 4 * TILE;              // A hi, A lo, B hi, B lo
-constexpr int AF = BT * MC * 8;              // fp32 A staging of one stage (cp.async target): 16 KB
+constexpr int AFS = MC + 4;                  // fp32 A staging row stride (160 B: 16-byte lane accesses spread banks)
+constexpr int AF = BT * AFS * 8;             // fp32 A staging of one stage (cp.async target): 20 KB
 constexpr int SMEM = 2 * STAGE + 2 * AF + 3 * BR * 16 + 64;
 constexpr int TMEM_COLS = 2 * NN;             // period accumulator X, running sum Y
 constexpr int PERIOD = 128;                  // stages per period: 768 MMA steps accumulate in X before X is added into Y
@@ -329,6 +173,12 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
 }
 }  // namespace tcg
 
+// Warp-specialised pipeline: warps 0-7 (producers) wait until the MMAs of stage s-2 have released buffer s & 1
+// (its `empty` mbarrier, armed by tcgen05.commit), fill it and arrive on its `full` mbarrier; warp 8 waits on
+// `full`, issues the stage's MMAs and commits them to `empty`.  Producers meet at a named barrier once per tap,
+// where two warps refresh the per-(row, tap) table two taps ahead.  At the end of each period of PERIOD stages the
+// producers wait for the period's MMAs, fold X into Y and arrive on `fold`, which the issuer waits on before the
+// next period's first MMA overwrites X.
 template <bool BPA>
 __global__ void __launch_bounds__(tcg::THREADS, 2)
 td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
@@ -336,12 +186,14 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     using namespace tcg;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
-    float2 *af = reinterpret_cast<float2 *>(smem + 2 * STAGE);   // [2][BT][MC] raw samples, one stage ahead
+    float2 *af = reinterpret_cast<float2 *>(smem + 2 * STAGE);   // [2][BT][AFS] raw samples, one stage ahead
     float4 *tab = reinterpret_cast<float4 *>(smem + 2 * STAGE + 2 * AF);  // [3][BR]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 2 * AF + 3 * BR * 16);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+    uint64_t *full = bars, *empty = bars + 2, *fold_bar = bars + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 5);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp < PRODUCERS / 32;
     const int th0 = blockIdx.x * BT, r0 = blockIdx.y * BR;
     const int n_az = p.n_az, L = p.L;
     const int chunks = L / MC;
@@ -356,8 +208,11 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&bars[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&bars[1])), "r"(1));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[i])), "r"(PRODUCERS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&empty[i])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(fold_bar)), "r"(PRODUCERS));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     auto tap_off = [&](int kk) -> int {
@@ -386,120 +241,133 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-
-    // X (columns 0..NN) takes the MMAs of one period; at the period's end every thread folds its lanes and columns
-    // of X into Y (columns NN..2NN) with round-to-nearest fp32 adds (tensor-core accumulation keeps a small
-    // one-sided error per step; over a period of 768 steps it stays near 1e-5 relative)
-    const int q = warp & 3, h = warp >> 2;
+    const int q = warp & 3, h = (warp >> 2) & 1;
     const uint32_t x_ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
     const uint32_t y_ta = x_ta + (uint32_t)NN;
     bool have_y = false;
-    auto fold = [&]() {                       // Y (+)= X, this warp's 32 lanes x 64 columns
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            float xv[16], yv[16];
-            ld16(x_ta + 16 * c, xv);
-            if (have_y) {
-                ld16(y_ta + 16 * c, yv);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) xv[j] += yv[j];
-            }
-            st16(y_ta + 16 * c, xv);
-        }
-        have_y = true;
-    };
-
-    // A copies of one stage: thread copies (and later converts) 4 pairs of samples: pair e = tid + THREADS*it,
-    // row t = 8 (e >> 4 ... ) + ((e >> 1) & 7), samples m = 4 ((e >> 4) & 3) + 2 (e & 1) .. +1; lanes 0-15 cover one
-    // core matrix (8 rows x 16 B) of the bf16 tiles, so the 8-byte stores are conflict-free
-    auto a_pair = [&](int it, int &t, int &m) {
-        const int e = tid + THREADS * it;
-        m = ((e >> 4) & 3) * 4 + (e & 1) * 2;
-        t = (e >> 6) * 8 + ((e >> 1) & 7);
-    };
-    auto prefetch_A = [&](int s2) {
-        const int kk2 = s2 / chunks, m02 = (s2 - kk2 * chunks) * MC;
-        const int base2 = pmod(th0 + tap_off(kk2), n_az);
-        float2 *dst = af + (s2 & 1) * (BT * MC);
-#pragma unroll
-        for (int it = 0; it < BT * MC / 2 / THREADS; ++it) {
-            int t, m;
-            a_pair(it, t, m);
-            int row = base2 + t;
-            if (wide) row = row >= n_az ? row - n_az : row;
-            else row %= n_az;
-            const unsigned d = saddr(dst + t * MC + m);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(X + (size_t)row * L + m02 + m)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    if (stages > 0) prefetch_A(0);
-
     bool ok = true;
-    for (int s = 0; s < stages && ok; ++s) {
-        const int b = s & 1;
-        uint8_t *st = stage_base + b * STAGE;
-        if (s >= 2) ok = wait_bar(&bars[b], (uint32_t)(((s - 2) >> 1) & 1));   // MMAs of stage s-2 done
-        if (!ok) break;
-        const int kk = s / chunks, m0 = (s - kk * chunks) * MC;
-        if (s + 1 < stages) {
-            prefetch_A(s + 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");           // this thread's copies of stage s
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        if (warp < 2 && s % chunks == 0 && kk + 2 < nk) build_tab(kk + 2);
-        // A: the thread's own 4 pairs of samples, split into the hi and lo tiles
-        const float2 *src = af + b * (BT * MC);
+
+    if (producer) {
+        // A copies of one stage: pair e = tid + PRODUCERS*it, row t, samples m, m+1 (see a_pair)
+        auto a_pair = [&](int it, int &t, int &m) {
+            const int e = tid + PRODUCERS * it;
+            m = ((e >> 4) & 3) * 4 + (e & 1) * 2;
+            t = (e >> 6) * 8 + ((e >> 1) & 7);
+        };
+        auto prefetch_A = [&](int s2) {
+            const int kk2 = s2 / chunks, m02 = (s2 - kk2 * chunks) * MC;
+            const int base2 = pmod(th0 + tap_off(kk2), n_az);
+            float2 *dst = af + (s2 & 1) * (BT * AFS);
 #pragma unroll
-        for (int it = 0; it < BT * MC / 2 / THREADS; ++it) {
-            int t, m;
-            a_pair(it, t, m);
-            const float4 a = *reinterpret_cast<const float4 *>(src + t * MC + m);
-            uint2 hi, lo;
-            split2(a.x, a.y, hi.x, lo.x);
-            split2(a.z, a.w, hi.y, lo.y);
-            *reinterpret_cast<uint2 *>(st + off(t, 2 * m)) = hi;
-            *reinterpret_cast<uint2 *>(st + TILE + off(t, 2 * m)) = lo;
-        }
-        // B: thread = (row r = 8 warp + (lane & 7), 4 samples 4 (lane >> 3) ..): coefficient x window x phasor by a
-        // recurrence over the 4 samples, written as rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes
-        // with r & 4 write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
-        {
-            const int r = 8 * warp + (lane & 7), c = lane >> 3;
-            const float4 t4 = tab[(kk % 3) * BR + r];
-            const int mb = m0 + 4 * c;
-            const float2 e0 = phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref);
-            float sn, cs;
-            sincospif(t4.z, &sn, &cs);
-            const float2 step = make_float2(cs, -sn);                        // exp(-j pi phi), one sample
-            float2 e = e0;
-            uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float wm = win ? __ldg(win + mb + i) : 1.f;
-                const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
-                split2(v.x, -v.y, re_hi[i], re_lo[i]);
-                split2(v.y, v.x, im_hi[i], im_lo[i]);
-                e = cmul(e, step);
+            for (int it = 0; it < BT * MC / 2 / PRODUCERS; ++it) {
+                int t, m;
+                a_pair(it, t, m);
+                int row = base2 + t;
+                if (wide) row = row >= n_az ? row - n_az : row;
+                else row %= n_az;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst + t * AFS + m)),
+                             "l"(X + (size_t)row * L + m02 + m) : "memory");
             }
-            const bool swap = (r & 4) != 0;
-            const int o_re = off(2 * r, 8 * c), o_im = off(2 * r + 1, 8 * c);
-            const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
-            const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
-            const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
-            const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
-            *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_im : o_re)) = swap ? ih : rh;
-            *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_im : o_re)) = swap ? il : rl;
-            *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_re : o_im)) = swap ? rh : ih;
-            *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_re : o_im)) = swap ? rl : il;
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        auto fold = [&]() {                   // Y (+)= X, this warp's 32 lanes x 64 columns
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float xv[16], yv[16];
+                ld16(x_ta + 16 * c, xv);
+                if (have_y) {
+                    ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) xv[j] += yv[j];
+                }
+                st16(y_ta + 16 * c, xv);
+            }
+            have_y = true;
+        };
+        if (stages > 0) prefetch_A(0);
+        for (int s = 0; s < stages; ++s) {
+            const int b = s & 1;
+            uint8_t *st = stage_base + b * STAGE;
+            // a wait that gives up clears ok and every later wait is skipped, but every thread still runs the loop
+            // to its end, so the named barriers stay matched (the tile then reads NaN)
+            if (s >= 2 && ok) ok = wait_bar(&empty[b], (uint32_t)(((s - 2) >> 1) & 1));
+            const int kk = s / chunks, m0 = (s - kk * chunks) * MC;
+            if (s % chunks == 0) {             // tap boundary: the table of tap kk-1 is no longer read
+                asm volatile("bar.sync 1, %0;" ::"n"(PRODUCERS) : "memory");
+                if (warp < 2 && kk + 2 < nk) build_tab(kk + 2);
+            }
+            if (s + 1 < stages) {
+                prefetch_A(s + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");       // this thread's copies of stage s
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            // A: the thread's own 4 pairs of samples, split into the hi and lo tiles
+            const float2 *src = af + b * (BT * AFS);
+#pragma unroll
+            for (int it = 0; it < BT * MC / 2 / PRODUCERS; ++it) {
+                int t, m;
+                a_pair(it, t, m);
+                const float4 a = *reinterpret_cast<const float4 *>(src + t * AFS + m);
+                uint2 hi, lo;
+                split2(a.x, a.y, hi.x, lo.x);
+                split2(a.z, a.w, hi.y, lo.y);
+                *reinterpret_cast<uint2 *>(st + off(t, 2 * m)) = hi;
+                *reinterpret_cast<uint2 *>(st + TILE + off(t, 2 * m)) = lo;
+            }
+            // B: thread = (row r = 8 warp + (lane & 7), samples 4 (lane >> 3) ..): coefficient x window x phasor by a
+            // recurrence over the 4 samples, rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes with r & 4
+            // write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
+            {
+                const int r = 8 * warp + (lane & 7), c = lane >> 3;
+                const float4 t4 = tab[(kk % 3) * BR + r];
+                const int mb = m0 + 4 * c;
+                const float2 e0 = phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref);
+                float sn, cs;
+                sincospif(t4.z, &sn, &cs);
+                const float2 step = make_float2(cs, -sn);                    // exp(-j pi phi), one sample
+                float2 e = e0;
+                uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float wm = win ? __ldg(win + mb + i) : 1.f;
+                    const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
+                    split2(v.x, -v.y, re_hi[i], re_lo[i]);
+                    split2(v.y, v.x, im_hi[i], im_lo[i]);
+                    e = cmul(e, step);
+                }
+                const bool swap = (r & 4) != 0;
+                const int o_re = off(2 * r, 8 * c), o_im = off(2 * r + 1, 8 * c);
+                const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+                const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+                const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+                const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_im : o_re)) = swap ? ih : rh;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_im : o_re)) = swap ? il : rl;
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_re : o_im)) = swap ? rh : ih;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_re : o_im)) = swap ? rl : il;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[b])) : "memory");
+            if ((s + 1) % PERIOD == 0 && s + 1 < stages) {   // end of a period: its MMAs done, fold X into Y
+                if (ok) ok = wait_bar(&empty[b], (uint32_t)((s >> 1) & 1));
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (ok) fold();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(fold_bar)) : "memory");
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        if (ok && stages > 0) ok = wait_bar(&empty[(stages - 1) & 1], (uint32_t)(((stages - 1) >> 1) & 1));
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else if (lane == 0) {                   // the MMA issuer
+        for (int s = 0; s < stages; ++s) {
+            const int b = s & 1;
+            if (ok) ok = wait_bar(&full[b], (uint32_t)((s >> 1) & 1));
+            if (ok && s % PERIOD == 0 && s > 0) ok = wait_bar(fold_bar, (uint32_t)((s / PERIOD - 1) & 1));
+            if (!ok) break;                       // the issuer meets no named barrier; producers time out on empty
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = saddr(st), a_lo = a_hi + TILE, b_hi = a_hi + 2 * TILE, b_lo = a_hi + 3 * TILE;
+            const uint32_t a_hi = saddr(stage_base + b * STAGE), a_lo = a_hi + TILE, b_hi = a_hi + 2 * TILE,
+                           b_lo = a_hi + 3 * TILE;
 #pragma unroll
             for (int ks = 0; ks < KR / 16; ++ks) {
                 const uint32_t ko = ks * 2 * LBO;                     // 16 K entries = two core-matrix columns
@@ -507,51 +375,47 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
                 mma(tmem, desc(a_hi + ko), desc(b_lo + ko), 1u);
                 mma(tmem, desc(a_lo + ko), desc(b_hi + ko), 1u);
             }
-            commit(&bars[b]);
-        }
-        if ((s + 1) % PERIOD == 0 && s + 1 < stages) {   // end of a period: wait for its MMAs, fold X into Y
-            ok = wait_bar(&bars[b], (uint32_t)((s >> 1) & 1));
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            fold();
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();                      // X is free for the next period's first MMA
+            commit(&empty[b]);
         }
     }
-    if (ok && stages > 0) ok = wait_bar(&bars[(stages - 1) & 1], (uint32_t)(((stages - 1) >> 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // accumulator -> registers: warp w reads TMEM lanes 32 (w % 4).. (pixels) and columns 64 (w / 4)..
+    // accumulator -> registers (producer warps): warp w reads TMEM lanes 32 (w % 4).. and columns 64 ((w / 4) % 2)..
     const int th = 32 * q + lane;
     float v[64];
-    if (ok && stages > 0) {
+    if (producer) {
+        if (ok && stages > 0) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            ld16(x_ta + 16 * c, v + 16 * c);
-            if (have_y) {
-                float yv[16];
-                ld16(y_ta + 16 * c, yv);
+            for (int c = 0; c < 4; ++c) {
+                ld16(x_ta + 16 * c, v + 16 * c);
+                if (have_y) {
+                    float yv[16];
+                    ld16(y_ta + 16 * c, yv);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[16 * c + j] += yv[j];
+                    for (int j = 0; j < 16; ++j) v[16 * c + j] += yv[j];
+                }
             }
-        }
-    } else {
-        const float f = ok ? 0.f : __int_as_float(0x7fc00000);   // no taps: zero; a wait that gave up: NaN
+        } else {
+            const float f = ok ? 0.f : __int_as_float(0x7fc00000);   // no taps: zero; a wait that gave up: NaN
 #pragma unroll
-        for (int j = 0; j < 64; ++j) v[j] = f;
+            for (int j = 0; j < 64; ++j) v[j] = f;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 
     const int G = gridDim.z;
+    bool writer = producer;
     if (G > 1) {                              // partial tiles parked in the stage buffers, rank 0 adds in rank order
         float *red = reinterpret_cast<float *>(smem);            // [128 columns][128 pixels] = 64 KB
         cg::cluster_group cluster = cg::this_cluster();
+        if (producer) {
 #pragma unroll
-        for (int j = 0; j < 64; ++j) red[(64 * h + j) * BT + th] = v[j];
+            for (int j = 0; j < 64; ++j) red[(64 * h + j) * BT + th] = v[j];
+        }
         cluster.sync();
-        if (cluster.block_rank() == 0) {
+        if (producer && cluster.block_rank() == 0) {
             for (int rk = 1; rk < G; ++rk) {
                 const float *rem = cluster.map_shared_rank(red, rk);
 #pragma unroll
@@ -559,10 +423,10 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             }
         }
         cluster.sync();
-        if (cluster.block_rank() != 0) return;
+        writer = producer && cluster.block_rank() == 0;
     }
     const int tcol = th0 + th;
-    if (tcol < n_az) {
+    if (writer && tcol < n_az) {
 #pragma unroll
         for (int j = 0; j < 64; j += 2) {
             const int r = r0 + (64 * h + j) / 2;
@@ -644,71 +508,8 @@ td_row_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
     }
 }
 
-// Cluster size for the tap split: the G (1 .. 8, at most K, at least 8 taps per rank unless G = 1) whose
-// clusters fill the co-resident cluster slots in the most nearly whole number of waves.
-template <bool BPA>
-int pick_cluster(int tiles, int K) {
-    static int cached_dev = -1, cached_tiles = -1, cached_K = -1, cached_G = 1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev == cached_dev && tiles == cached_tiles && K == cached_K) return cached_G;
-    int best_G = 1;
-    double best = -1.0;
-    for (int G = 1; G <= TD_MAX_CLUSTER; ++G) {
-        if (G > 1 && (K < 8 * G)) break;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3(1, 1, G);
-        cfg.blockDim = dim3(TD_THREADS);
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = G;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, td_tile_kernel<BPA>, &cfg) != cudaSuccess || clusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
-        const double waves = (double)tiles / clusters;
-        const double eff = waves / std::ceil(waves);
-        if (eff > best + 1e-3) {
-            best = eff;
-            best_G = G;
-        }
-    }
-    cached_dev = dev;
-    cached_tiles = tiles;
-    cached_K = K;
-    cached_G = best_G;
-    return best_G;
-}
-
-template <bool BPA>
-rosar_status launch_tiles(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p,
-                          int K, float2 *out, cudaStream_t s) {
-    const int gx = (p.n_az + TD_BT - 1) / TD_BT, gy = (p.n_rng + TD_BR - 1) / TD_BR;
-    const int G = pick_cluster<BPA>(gx * gy, K);
-    const int k_per = (K + G - 1) / G;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(gx, gy, G);
-    cfg.blockDim = dim3(TD_THREADS);
-    cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = G;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tile_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
-    if (e != cudaSuccess)
-        return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", BPA ? "bpa_time" : "sas_time", cudaGetErrorString(e));
-    return check_launch(BPA ? "bpa_time" : "sas_time");
-}
-
-// Cluster size for the tensor-core kernel, as pick_cluster (its own occupancy: dynamic shared memory, 256 threads).
+// Cluster size for the tap split: the G (1 .. 8, at most K/4) whose clusters fill the co-resident cluster slots
+// in the most nearly whole number of waves (occupancy of the tensor-core kernel: its shared memory and threads).
 template <bool BPA>
 int pick_cluster_tc(int tiles, int K) {
     static int cached_dev = -1, cached_tiles = -1, cached_K = -1, cached_G = 1;
