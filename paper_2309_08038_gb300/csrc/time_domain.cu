@@ -585,7 +585,7 @@ rosar_status launch_time_domain(const float2 *raw, const float *win, const float
                                 int o_row_stride, const TdParams &p, int K, bool bpa, float2 *out, cudaStream_t s) {
     if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: L=%d is not a multiple of %d", p.L, TD_MC);
     if (bpa || o_row_stride == 0) {
-        if ((p.n_rng + TD_BR - 1) / TD_BR > 65535)
+        if ((p.n_rng + tcg::BR - 1) / tcg::BR > 65535)
             return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
         return bpa ? launch_tc<true>(raw, win, w, o, p, K, out, s) : launch_tc<false>(raw, win, w, o, p, K, out, s);
     }
