@@ -19,7 +19,7 @@
 // depends on (r, d) only; that kernel variant tabulates (x, alpha*phase) per d
 // and the pixel loop is two gathers, an interpolation and a complex MAC.
 //
-// Grid: (azimuth tiles of 256 pixels, rows).  Compute-bound (FP32 + SFU).
+// Grid: (azimuth tiles of 256 pixels, rows).  Compute-bound (FP32 + SFU) once S is staged in shared memory.
 
 #include "rosar_internal.cuh"
 
@@ -28,18 +28,28 @@ namespace {
 
 constexpr int BPA_THREADS = 256;
 constexpr int BPA_DC = 512;   // aperture offsets staged per chunk
+constexpr int BPA_WR = 6;     // range rows of the staged S window
+constexpr int BPA_WC = BPA_THREADS + BPA_DC;   // columns (pulses) of the window
+constexpr int BPA_SMEM = BPA_WR * BPA_WC * 8;  // 36 KB
 
 __device__ __forceinline__ float2 read_bin(const float2 *__restrict__ S, int l, int L, size_t col, int n_az) {
     return (l >= 0 && l < L) ? __ldg(S + (size_t)l * n_az + col) : make_float2(0.f, 0.f);
 }
 
+// Per chunk of offsets the bins a pixel of row r reads lie in a few rows near r (x = r + (R_n - rho)/dR, within a
+// couple of bins over a +-30 degree aperture): the rows [wlo, wlo + BPA_WR) around the chunk's nominal range of x
+// (one bin of margin each side) and the pulses th0 + dc .. th0 + dc + BPA_WC are staged in shared memory once, and
+// every (pixel, pulse) sample whose two bins fall in the window reads it there (others, e.g. under large supplied
+// position errors, read S through L2 as before).
 template <bool NOMINAL>
 __global__ void __launch_bounds__(BPA_THREADS)
 bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ dphi, const float *__restrict__ dr,
            int L, int n_az, int M_ap, int interp, float2 *__restrict__ out) {
-    __shared__ float4 dtab[BPA_DC];                           // NOMINAL: (x, a.re, a.im, -); else (sin, cos, -, -)
+    extern __shared__ float2 wsm[];                           // [BPA_WR][BPA_WC]
+    __shared__ float4 dtab[BPA_DC];                           // NOMINAL: (x, a.re, a.im, -); else (sin, cos, x_nominal, -)
     __shared__ float4 ptab[NOMINAL ? 1 : BPA_THREADS + BPA_DC];   // per pulse (cos(eps/2), sin(eps/2), dr, -)
     __shared__ float2 rowph;
+    __shared__ float red_lo[BPA_THREADS / 32], red_hi[BPA_THREADS / 32];
 
     const int r = blockIdx.y;
     const int th0 = blockIdx.x * BPA_THREADS;
@@ -62,28 +72,33 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
     for (int dc = d_beg; dc < d_end; dc += BPA_DC) {
         const int nd = min(BPA_DC, d_end - dc);
         __syncthreads();
+        float xlo = 1e30f, xhi = -1e30f;
         for (int i = threadIdx.x; i < nd; i += BPA_THREADS) {
             float s, c;
             sincospif((float)(dc + i) / (float)n_az, &s, &c);   // sin/cos(pi*d/n_az)
+            // nominal geometry: x and the weight of this offset
+            const float s2 = s * s;
+            const float num = 4.f * R * r0 * s2;                // R_n^2 - rho^2
+            const float Rn2 = fmaf(rho, rho, num);
+            float delta, alpha;
+            if (Rn2 > 0.f) {
+                const float inv = rsqrtf(Rn2);
+                const float Rn = Rn2 * inv;
+                delta = __fdividef(num, Rn + rho);
+                alpha = fmaxf(0.f, fmaf(-2.f * R, s2, rho) * inv);
+            } else {
+                delta = 0.f;
+                alpha = 1.f;
+            }
+            const float x = fmaf(delta, p.inv_dR, rf);
+            xlo = fminf(xlo, x);
+            xhi = fmaxf(xhi, x);
             if (NOMINAL) {
-                const float s2 = s * s;
-                const float num = 4.f * R * r0 * s2;            // R_n^2 - rho^2
-                const float Rn2 = fmaf(rho, rho, num);
-                float delta, alpha;
-                if (Rn2 > 0.f) {
-                    const float inv = rsqrtf(Rn2);
-                    const float Rn = Rn2 * inv;
-                    delta = __fdividef(num, Rn + rho);
-                    alpha = fmaxf(0.f, fmaf(-2.f * R, s2, rho) * inv);
-                } else {
-                    delta = 0.f;
-                    alpha = 1.f;
-                }
                 float ps, pc;
                 sincospif(2.f * p.two_f_over_c * delta, &ps, &pc);
-                dtab[i] = make_float4(fmaf(delta, p.inv_dR, rf), alpha * pc, -alpha * ps, 0.f);
+                dtab[i] = make_float4(x, alpha * pc, -alpha * ps, 0.f);
             } else {
-                dtab[i] = make_float4(s, c, 0.f, 0.f);
+                dtab[i] = make_float4(s, c, x, 0.f);
             }
         }
         if (!NOMINAL) {
@@ -95,10 +110,38 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                 ptab[i] = make_float4(ce, se, dr ? __ldg(dr + n) : 0.f, 0.f);
             }
         }
+        // window rows from the chunk's nominal x range
+#pragma unroll
+        for (int sft = 16; sft > 0; sft >>= 1) {
+            xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, sft));
+            xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, sft));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red_lo[threadIdx.x >> 5] = xlo;
+            red_hi[threadIdx.x >> 5] = xhi;
+        }
+        __syncthreads();
+        xlo = red_lo[0];
+        xhi = red_hi[0];
+        for (int i = 1; i < BPA_THREADS / 32; ++i) {
+            xlo = fminf(xlo, red_lo[i]);
+            xhi = fmaxf(xhi, red_hi[i]);
+        }
+        const int wlo = max(0, (int)floorf(xlo) - 1);
+        const int whi = min(L - 1, (int)floorf(xhi) + 2);            // last staged row
+        const int nrow = min(BPA_WR, whi - wlo + 1);
+        const int wtop = wlo + nrow;                                  // rows [wlo, wtop) staged
+        const int ncol = BPA_THREADS + nd;
+        for (int e = threadIdx.x; e < nrow * ncol; e += BPA_THREADS) {
+            const int rr = e / ncol, cc = e - rr * ncol;
+            const int n = pmod(th0 + dc + cc, n_az);
+            wsm[rr * BPA_WC + cc] = __ldg(S + (size_t)(wlo + rr) * n_az + n);
+        }
         __syncthreads();
         if (th < n_az) {
             int n = th + dc;
             n = n < 0 ? n + n_az : (n >= n_az ? n - n_az : n);
+#pragma unroll 4
             for (int i = 0; i < nd; ++i) {
                 const float4 t = dtab[i];
                 float x;
@@ -129,16 +172,24 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                     x = fmaf(delta, p.inv_dR, rf);
                     a = make_float2(alpha * pc, -alpha * ps);
                 }
+                const int col = threadIdx.x + i;
                 float2 sv;
                 if (interp) {
                     const float fl = floorf(x);
                     const int l0 = (int)fl;
                     const float f = x - fl;
-                    const float2 s0 = read_bin(S, l0, L, n, n_az);
-                    const float2 s1 = read_bin(S, l0 + 1, L, n, n_az);
+                    float2 s0, s1;
+                    if (l0 >= wlo && l0 + 1 < wtop) {
+                        s0 = wsm[(l0 - wlo) * BPA_WC + col];
+                        s1 = wsm[(l0 + 1 - wlo) * BPA_WC + col];
+                    } else {
+                        s0 = read_bin(S, l0, L, n, n_az);
+                        s1 = read_bin(S, l0 + 1, L, n, n_az);
+                    }
                     sv = make_float2(fmaf(f, s1.x - s0.x, s0.x), fmaf(f, s1.y - s0.y, s0.y));
                 } else {
-                    sv = read_bin(S, (int)floorf(x + 0.5f), L, n, n_az);
+                    const int l0 = (int)floorf(x + 0.5f);
+                    sv = (l0 >= wlo && l0 < wtop) ? wsm[(l0 - wlo) * BPA_WC + col] : read_bin(S, l0, L, n, n_az);
                 }
                 cmac(acc, a, sv);
                 if (++n == n_az) n = 0;
@@ -154,10 +205,15 @@ rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, 
                         int n_az, int M_ap, int interp, float2 *out, cudaStream_t s) {
     if (n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "bpa: n_rng=%d exceeds 65535", n_rng);
     dim3 grid((n_az + BPA_THREADS - 1) / BPA_THREADS, n_rng);
-    if (dphi == nullptr && dr == nullptr)
-        bpa_kernel<true><<<grid, BPA_THREADS, 0, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
+    static int done[2][kMaxDevices] = {};
+    const bool nominal = dphi == nullptr && dr == nullptr;
+    rosar_status st = nominal ? ensure_smem((const void *)bpa_kernel<true>, BPA_SMEM, done[0], "bpa")
+                              : ensure_smem((const void *)bpa_kernel<false>, BPA_SMEM, done[1], "bpa");
+    if (st != ROSAR_OK) return st;
+    if (nominal)
+        bpa_kernel<true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
     else
-        bpa_kernel<false><<<grid, BPA_THREADS, 0, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
+        bpa_kernel<false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
     return check_launch("bpa");
 }
 
