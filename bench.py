@@ -481,7 +481,7 @@ def run_ours(args):
                                   "algorithmic_bytes": k2_bytes, "gbs": k2_bytes / t_k2 / 1e9,
                                   "hbm_frac": k2_bytes / t_k2 / 1e9 / hbm},
     }
-    fft_name = "azimuth_fft_fixed_kernel<256, 3600, 16, 5, 5, 3, 3>"     # the compile-time plan of 3600-pulse rows
+    fft_name = "azimuth_fft_fixed_kernel<256, 3600, 16, 15, 15>"     # the compile-time plan of 3600-pulse rows
     if fft_ok:
         kernels[fft_name] = {
             "us_per_launch": t_k2f * 1e6, "algorithmic_bytes": k2f_bytes, "gbs": k2f_bytes / t_k2f / 1e9,

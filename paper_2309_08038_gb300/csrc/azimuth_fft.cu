@@ -11,8 +11,8 @@
 //
 // One CTA owns one range row, staged in shared memory (one pad element per 16
 // against bank conflicts).  The forward transform is an in-place mixed-radix
-// decimation-in-frequency FFT (radices 16, 8, 4, 2, 5, 3; N = 2^a 3^b 5^c <= 16384;
-// a planner picks the sequence with the fewest passes, e.g. 3600 = 16*5*5*3*3).
+// decimation-in-frequency FFT (radices 16, 8, 4, 2, 5, 3 and a prime-factor 15; N = 2^a 3^b 5^c <= 16384;
+// a planner picks the sequence with the fewest passes, e.g. 3600 = 16*15*15).
 // Every butterfly reads and writes the same R slots, so only its own R values are
 // live and passes need one barrier each; its twiddles are powers of one table entry.  It leaves the spectrum in digit-reversed
 // order; H is produced by the same transform (so it is stored in that order), the
@@ -99,14 +99,27 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
                [&](float2 *x, const float2 *tc, const float2 *tf) { row_dit(x, N, pl, tc, tf); });
 }
 
-// Compile-time plan for one row length (T threads, no padding: N has an odd factor).
+// Compile-time plan for one row length (T threads, no padding: N has an odd factor, H staged): the first pass
+// reads S from global memory, the last writes the image, and the last forward pass, the product with H and
+// the first inverse pass run as one step (row_filter_fused): four barriers for 16.15.15.
 template <int T, int N, int... R>
-__global__ void __launch_bounds__(T, 1)
+__global__ void __launch_bounds__(T, (T <= 256 ? 2 : 1))
 azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, Layout lay, RowMap map,
                          float2 *__restrict__ out) {
-    row_filter(S, H, N, pad_shift_for(N), lay, map, out,
-               [](float2 *x, const float2 *tc, const float2 *tf) { dif_seq<N, N, false, T, R...>(x, tc, tf); },
-               [](float2 *x, const float2 *tc, const float2 *tf) { dit_seq<N, N, false, T, R...>(x, tc, tf); });
+    extern __shared__ float2 sm[];
+    float2 *x = sm;
+    float2 *hb = x + padded_len(N);
+    float2 *tw = hb + padded_len(N);
+    const size_t row = (size_t)blockIdx.x * N;
+    const size_t hrow = (size_t)(blockIdx.x % map.h_rows) * N;
+    for (int n = threadIdx.x; n < N; n += T) cp_async8(hb + n, H + hrow + n);
+    cp_async_commit();
+    const float2 *tc, *tf;
+    build_twiddles(N, false, tw, &tc, &tf);
+    cp_async_wait<0>();
+    __syncthreads();
+    griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
+    row_filter_fused<N, T, true, R...>(S + row, hb, map.conj_h ? -1.f : 1.f, x, out + row, tc, tf);
 }
 
 template <int MAXT>
@@ -235,12 +248,12 @@ namespace {
 
 // Launches the compile-time-plan kernel when the run-time planner picks exactly its radices for n_az (so H,
 // made by the run-time plan, is in the same order); returns false to fall back to the run-time plan.
-template <int N, int... R>
+template <int T, int N, int... R>
 bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, RowMap map, bool ov, const float2 *S,
                const float2 *H, float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
-    constexpr int T = 256;
     constexpr int rad[] = {R...};
-    if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pl.npass != (int)sizeof...(R))
+    if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pad_shift_for(N) != 31 ||
+        !lay.stage_h || pl.npass != (int)sizeof...(R))
         return false;
     for (int i = 0; i < pl.npass; ++i)
         if (pl.rad[i] != rad[i]) return false;
@@ -277,9 +290,10 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     {
         cudaError_t fle = cudaSuccess;
         rosar_status fst = ROSAR_OK;
-        if (try_fixed<3600, 16, 5, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<1800, 8, 5, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<360, 8, 5, 3, 3>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst)) {
+        if (try_fixed<256, 3600, 16, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<256, 1800, 8, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<512, 7200, 8, 4, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<256, 360, 8, 3, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst)) {
             if (fst == ROSAR_OK && fle != cudaSuccess)
                 return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(fle));
             return fst;

@@ -67,8 +67,10 @@ __device__ __forceinline__ void run_range(const ScanDev &sc, int n0, char *sm, b
 }
 
 // One range row of a scan through the frequency-domain azimuth filter (same arithmetic as
-// rosar_sparse_azimuth_fft).  S was written by this kernel's range tiles: read through L2 (ld.cg),
-// eight loads in flight per thread.
+// rosar_sparse_azimuth_fft).  S was written by this kernel's range tiles: read through L2 (ld.cg).  The row
+// lengths with a compile-time plan run the fused filter (first and last passes on global memory, H read from
+// global in the fused middle step); the others load the row, eight loads in flight per thread, and run the
+// run-time plan.
 __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem) {
     const int N = sc.n_az;
     float2 *x = reinterpret_cast<float2 *>(smem);
@@ -77,6 +79,16 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
     rowfft::build_twiddles(N, false, tw, &tc, &tf);
     const size_t row = (size_t)r * N;
     const float2 *Srow = sc.S + row;
+    if (sc.fixed) {
+        __syncthreads();
+        switch (sc.fixed) {                   // the run-time plan's radices, constant strides
+            case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
+            case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
+            default: rowfft::row_filter_fused<7200, BT_THREADS, false, 8, 4, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
+        }
+        __syncthreads();
+        return;
+    }
     for (int n0 = threadIdx.x; n0 < N; n0 += 8 * BT_THREADS) {
         float2 v[8];
 #pragma unroll
@@ -91,23 +103,13 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
         }
     }
     __syncthreads();
-    switch (sc.fixed) {                       // same passes as the run-time plan, constant strides
-        case 1: rowfft::dif_seq<1800, 1800, false, BT_THREADS, 8, 5, 5, 3, 3>(x, tc, tf); break;
-        case 2: rowfft::dif_seq<3600, 3600, false, BT_THREADS, 16, 5, 5, 3, 3>(x, tc, tf); break;
-        case 3: rowfft::dif_seq<7200, 7200, false, BT_THREADS, 8, 4, 5, 5, 3, 3>(x, tc, tf); break;
-        default: rowfft::row_dif(x, N, sc.plan, tc, tf);
-    }
+    rowfft::row_dif(x, N, sc.plan, tc, tf);
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
         const float2 y = cmul(__ldg(sc.H + row + n), x[rowfft::rpad(n, sc.plan.pad_shift)]);
         x[rowfft::rpad(n, sc.plan.pad_shift)] = make_float2(y.x, -y.y);
     }
     __syncthreads();
-    switch (sc.fixed) {
-        case 1: rowfft::dit_seq<1800, 1800, false, BT_THREADS, 8, 5, 5, 3, 3>(x, tc, tf); break;
-        case 2: rowfft::dit_seq<3600, 3600, false, BT_THREADS, 16, 5, 5, 3, 3>(x, tc, tf); break;
-        case 3: rowfft::dit_seq<7200, 7200, false, BT_THREADS, 8, 4, 5, 5, 3, 3>(x, tc, tf); break;
-        default: rowfft::row_dit(x, N, sc.plan, tc, tf);
-    }
+    rowfft::row_dit(x, N, sc.plan, tc, tf);
     for (int n = threadIdx.x; n < N; n += BT_THREADS) {
         const float2 y = x[rowfft::rpad(n, sc.plan.pad_shift)];
         sc.out[row + n] = make_float2(y.x, -y.y);
@@ -200,9 +202,9 @@ KernelFn kernel_for(int J) {
 
 // The compile-time plans fft_row_tile carries, used only when the run-time planner picks the same radices.
 int fixed_plan_code(int n_az, const rowfft::RowPlan &pl) {
-    static const int r1800[] = {8, 5, 5, 3, 3}, r3600[] = {16, 5, 5, 3, 3}, r7200[] = {8, 4, 5, 5, 3, 3};
+    static const int r1800[] = {8, 15, 15}, r3600[] = {16, 15, 15}, r7200[] = {8, 4, 15, 15};
     const int *rad = n_az == 1800 ? r1800 : n_az == 3600 ? r3600 : n_az == 7200 ? r7200 : nullptr;
-    const int np = n_az == 7200 ? 6 : 5;
+    const int np = n_az == 7200 ? 4 : 3;
     if (!rad || pl.npass != np || pl.pad_shift != rowfft::pad_shift_for(n_az)) return 0;
     for (int i = 0; i < np; ++i)
         if (pl.rad[i] != rad[i]) return 0;

@@ -81,6 +81,31 @@ __device__ __forceinline__ void small_dft<5>(float2 *v) {
     v[3] = make_float2(a2.x - b2.y, a2.y + b2.x);              // a2 + i b2
 }
 
+// 15 = 3 x 5 by the prime-factor (Good-Thomas) index maps, which need no twiddles between the two sets of
+// small DFTs: input n = (5 n1 + 3 n2) mod 15, output k = (10 k1 + 6 k2) mod 15 (10 = 1 mod 3 and 0 mod 5,
+// 6 = 0 mod 3 and 1 mod 5), so that W_15^(nk) = W_3^(n1 k1) W_5^(n2 k2).
+template <>
+__device__ __forceinline__ void small_dft<15>(float2 *v) {
+    float2 a[5][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; ++n2)
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1) a[n2][n1] = v[(5 * n1 + 3 * n2) % 15];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; ++n2) small_dft<3>(a[n2]);
+    float2 b[3][5];
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+        for (int n2 = 0; n2 < 5; ++n2) b[k1][n2] = a[n2][k1];
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) small_dft<5>(b[k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 5; ++k2) v[(10 * k1 + 6 * k2) % 15] = b[k1][k2];
+}
+
 template <int R>
 __device__ __forceinline__ void pow2_dft(float2 *v) {
     fft::dft_dif<R>(v);                     // output index r sits at v[brev(r)]
@@ -128,7 +153,7 @@ using fft::twiddle_powers;
 template <int R, bool PAD>
 __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     const int s = M / R, tstep = N / M, nb = N / R, nblk = N / M;
-    const bool by_blk = !PAD && nblk >= 32 && (M & 1);     // as butterfly_index: odd lane strides
+    const bool by_blk = !PAD && nblk >= 16 && (M & 1);     // as butterfly_index: odd lane strides
     const float inv_d = 1.f / (float)(by_blk ? nblk : s);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
         const int q = quot(idx, inv_d);
@@ -151,7 +176,7 @@ __device__ __forceinline__ void dif_pass(float2 *x, int N, int M, const float2 *
 template <int R, bool PAD>
 __device__ __forceinline__ void dit_pass(float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     const int s = M / R, tstep = N / M, nb = N / R, nblk = N / M;
-    const bool by_blk = !PAD && nblk >= 32 && (M & 1);     // as butterfly_index: odd lane strides
+    const bool by_blk = !PAD && nblk >= 16 && (M & 1);     // as butterfly_index: odd lane strides
     const float inv_d = 1.f / (float)(by_blk ? nblk : s);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
         const int q = quot(idx, inv_d);
@@ -177,6 +202,7 @@ template <bool DIF, bool PAD>
 __device__ __forceinline__ void stage(int R, float2 *x, int N, int M, const float2 *tc, const float2 *tf) {
     switch (R) {
         ROSAR_STAGE_CASE(16)
+        ROSAR_STAGE_CASE(15)
         ROSAR_STAGE_CASE(8)
         ROSAR_STAGE_CASE(5)
         ROSAR_STAGE_CASE(4)
@@ -193,12 +219,12 @@ template <int... R>
 struct Radices {};
 
 // Butterfly idx of a pass with nblk = N/M blocks of s = M/R butterflies: blocks vary fastest across threads
-// when a warp spans at least 32 blocks of odd length M (lanes then stride by M: distinct banks, and the lanes
-// share one twiddle), else positions within a block vary fastest.
+// when there are at least 16 blocks of odd length M (the 16 lanes of a 64-bit shared-memory phase then stride
+// by M: distinct bank pairs, and the lanes share one twiddle), else positions within a block vary fastest.
 template <int N, int M, int R>
 __device__ __forceinline__ void butterfly_index(int idx, int &blk, int &j) {
     constexpr int s = M / R, nblk = N / M;
-    if constexpr (nblk >= 32 && (M & 1)) {
+    if constexpr (nblk >= 16 && (M & 1)) {
         j = idx / nblk;
         blk = idx - j * nblk;
     } else {
@@ -263,6 +289,100 @@ __device__ __forceinline__ void dit_seq(float2 *x, const float2 *tc, const float
     dit_pass_c<N, M, R, PAD, T>(x, tc, tf);
 }
 
+// The whole row filter conj(DIT(conj(H . DIF(src)))) with the first and last passes on global memory and the
+// last forward pass, the product with H and the first inverse pass fused into one step: per element four
+// shared-memory round trips fewer than loading the row, running dif_seq, multiplying and running dit_seq, with
+// the same arithmetic (the two fused passes act on blocks of one butterfly, whose twiddles are 1).
+
+// First DIF pass (M = N, stride s = N/R) with its inputs read from global memory (ld.cg: src may have been
+// written earlier by the same kernel).
+template <int N, int R, int T>
+__device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src, float2 *x, const float2 *tc,
+                                                 const float2 *tf) {
+    constexpr int s = N / R;
+#pragma unroll 1
+    for (int j = threadIdx.x; j < s; j += T) {
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcg(src + j + r * s);
+        small_dft<R>(v);
+        x[j] = v[0];
+        float2 wq[R];
+        twiddle_powers<R>(twiddle(j, tc, tf), wq);
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[j + q * s] = cmul(v[q], wq[q]);
+    }
+    __syncthreads();
+}
+
+// Last forward pass (blocks of R, stride 1), y = conj(H . X) (conj(H) . X conjugated when hs = -1), and the
+// first pass of the inverse on the same block.  H is in the forward transform's digit-reversed order; h is
+// shared memory (H_SMEM) or global.
+template <int N, int R, int T, bool H_SMEM>
+__device__ __forceinline__ void fused_mid(float2 *x, const float2 *h, float hs) {
+    constexpr int nb = N / R;
+#pragma unroll 1
+    for (int b = threadIdx.x; b < nb; b += T) {
+        const int base = b * R;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[base + r];
+        small_dft<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 hv = H_SMEM ? h[base + r] : __ldg(h + base + r);
+            hv.y *= hs;
+            const float2 y = cmul(hv, v[r]);
+            v[r] = make_float2(y.x, -y.y);
+        }
+        small_dft<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[base + r] = v[r];
+    }
+    __syncthreads();
+}
+
+// Last DIT pass (M = N) written to global memory with the final conjugation of the inverse.
+template <int N, int R, int T>
+__device__ __forceinline__ void dit_last_global(const float2 *x, float2 *__restrict__ dst, const float2 *tc,
+                                                const float2 *tf) {
+    constexpr int s = N / R;
+#pragma unroll 1
+    for (int j = threadIdx.x; j < s; j += T) {
+        float2 v[R], wq[R];
+        twiddle_powers<R>(twiddle(j, tc, tf), wq);
+        v[0] = x[j];
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmul(x[j + q * s], wq[q]);
+        small_dft<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[j + r * s] = make_float2(v[r].x, -v[r].y);
+    }
+}
+
+template <int N, int M, int T, bool H_SMEM, int R, int... Rest>
+__device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float hs, const float2 *tc, const float2 *tf) {
+    if constexpr (sizeof...(Rest) == 0) {
+        static_assert(M == R, "the last radix spans the last block");
+        fused_mid<N, R, T, H_SMEM>(x, h, hs);
+    } else {
+        dif_pass_c<N, M, R, false, T>(x, tc, tf);
+        filter_middle<N, M / R, T, H_SMEM, Rest...>(x, h, hs, tc, tf);
+        dit_pass_c<N, M, R, false, T>(x, tc, tf);
+    }
+}
+
+// src, dst: the row in global memory (natural order); x: N elements of shared memory (no padding); the
+// caller has built the twiddle table and synchronised.  No barrier at the end.
+template <int N, int T, bool H_SMEM, int R1, int... Rs>
+__device__ __forceinline__ void row_filter_fused(const float2 *__restrict__ src, const float2 *h, float hs, float2 *x,
+                                                 float2 *__restrict__ dst, const float2 *tc, const float2 *tf) {
+    static_assert(sizeof...(Rs) >= 1, "at least two passes");
+    dif_first_global<N, R1, T>(src, x, tc, tf);
+    filter_middle<N, N / R1, T, H_SMEM, Rs...>(x, h, hs, tc, tf);
+    dit_last_global<N, R1, T>(x, dst, tc, tf);
+}
+
 // Forward DFT of the row, output in digit-reversed order.
 template <bool PAD>
 __device__ __forceinline__ void row_dif_t(float2 *x, int N, const RowPlan &pl, const float2 *tc, const float2 *tf) {
@@ -322,11 +442,11 @@ __device__ __forceinline__ void build_twiddles(int N, bool full, float2 *tw, con
 
 inline int threads_for(int N) { return N <= 4096 ? 256 : N <= 8192 ? 512 : 1024; }
 
-// Radix sequence for N over radices {16, 8, 4, 2, 5, 3}: fewest passes, then fewest butterflies per thread.
-// (Larger composite radices 6..15 shorten the sequence but lengthen each thread's serial chain; with the
-// few warps one row per CTA leaves per SM they measured slower on the 3600-pulse rows.)
+// Radix sequence for N over radices {16, 8, 4, 2, 5, 3, 15}: fewest passes, then fewest butterflies per thread
+// (the first radix found wins a tie).  15 is a prime-factor butterfly without inner twiddles, so a row with
+// a factor 225 takes two passes for it instead of four: 3600 = 16.15.15, 1800 = 8.15.15, 7200 = 8.4.15.15.
 inline bool make_plan(int N, RowPlan *pl) {
-    static const int kRad[] = {16, 8, 4, 2, 5, 3};
+    static const int kRad[] = {16, 8, 4, 2, 5, 3, 15};
     if (N < 2 || N > AF_MAX_N) return false;
     static std::mutex mu;
     static std::map<int, RowPlan> cache;
