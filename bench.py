@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--gather", action="store_true", help="time the gather-MAC azimuth path instead of the FFT form")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-form comparison")
     ap.add_argument("--batch-scans", type=int, default=256, help="scans in the batched comparison (a prefix of the 256)")
+    ap.add_argument("--per-scan", action="store_true",
+                    help="time one rosar_image_fft call per scan instead of the pipelined multi-scan call")
     return ap.parse_args()
 
 
@@ -175,11 +177,13 @@ def indoor_inputs(torch, device, rank):
     o = synth.draw_offsets(cfg)
     w = synth.default_weights(cfg, o)
     win = synth.hann_window(cfg.L)
-    raws = []
+    # N_BUF distinct scans, contiguous [N_BUF][n_az][L]: the same scene seen from a rotated start angle
+    # (a circular shift of the pulses); raws[b] are views of the stack
+    stack = torch.empty((N_BUF, cfg.n_az, cfg.L), dtype=torch.complex64, device=device)
     for b in range(N_BUF):
-        # distinct scans: the same scene seen from a rotated start angle (a circular shift of the pulses)
-        raws.append(torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, scan_rotation(b, rank), axis=0))).to(device))
-    return cfg, sc, raws, torch.from_numpy(w).to(device), torch.from_numpy(o).to(device), \
+        stack[b].copy_(torch.from_numpy(np.ascontiguousarray(np.roll(sc.raw, scan_rotation(b, rank), axis=0))))
+    raws = [stack[b] for b in range(N_BUF)]
+    return cfg, sc, stack, raws, torch.from_numpy(w).to(device), torch.from_numpy(o).to(device), \
         torch.from_numpy(win).to(device)
 
 
@@ -407,10 +411,12 @@ def run_ours(args):
     rosar.load()
     stream = torch.cuda.current_stream()
 
-    cfg, sc, raws, w, o, win = indoor_inputs(torch, device, rank)
+    cfg, sc, raw_stack, raws, w, o, win = indoor_inputs(torch, device, rank)
     px = cfg.L * cfg.n_az
     S_bufs = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(N_BUF)]
-    outs = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(N_BUF)]
+    out_stack = torch.empty((N_BUF, cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
+    outs = [out_stack[b] for b in range(N_BUF)]
+    ws2 = torch.empty((2, cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
     assert N_BUF * 3 * px * 8 > 2 * L2_BYTES
 
     # azimuth path picked by the autotuner (timed on this GPU, cached); the frequency-domain plan
@@ -434,13 +440,30 @@ def run_ours(args):
         else:
             rosar.image(raws[b], win, w, o, workspace=S_bufs[b], out=outs[b])
 
+    # headline step: one scan.  Where a pipelined plan exists, the timed scans go through rosar_image_fft_scans
+    # calls over the N_BUF resident scans (consecutive scans overlapped: N_BUF + 1 launches per call), replayed
+    # from CUDA graphs; otherwise one rosar_image_fft call per scan (2 launches), N_BUF calls per graph.
+    pipelined = fft_ok and rosar.image_fft_scans_pipelined(cfg.L, cfg.n_az) and not args.per_scan
+
+    def scans_call(n):
+        rosar.image_fft_scans(raw_stack[:n], win, H, workspace=ws2, out=out_stack[:n])
+
     peaks, peak_src = measured_peaks()
-    for i in range(args.warmup):                   # eager warm-up steps, then graph capture of N_BUF steps
+    for i in range(args.warmup):                   # eager warm-up steps, then graph capture
         image_step(i % N_BUF)
     torch.cuda.synchronize()
+    reps, rem = divmod(args.steps, N_BUF)
     with ClockSampler(local) as clk:
-        ms, wall = graph_loop(torch, lambda i: image_step(i % N_BUF), args.steps, args.warmup, N_BUF, stream, world,
-                              device)
+        if pipelined:
+            g_full = graph_of(torch, lambda i: scans_call(N_BUF), 1)
+            g_rem = graph_of(torch, lambda i: scans_call(rem), 1) if rem else None
+            ms, wall = time_loop(torch, lambda i: (g_full if i < reps else g_rem).replay(), reps + (1 if rem else 0),
+                                 max(1, -(-args.warmup // N_BUF)), stream, world, device)
+            launches = reps * (N_BUF + 1) + (rem + 1 if rem else 0)
+        else:
+            ms, wall = graph_loop(torch, lambda i: image_step(i % N_BUF), args.steps, args.warmup, N_BUF, stream,
+                                  world, device)
+            launches = 2 * args.steps
     ms_step = ms / args.steps
     value = world * px / (ms_step * 1e-3)
 
@@ -489,7 +512,29 @@ def run_ours(args):
             "traffic": recorded_traffic("azimuth_fft_fixed_kernel<3600>", "indoor",
                                         source_hash("azimuth_fft.cu", "row_fft.cuh", "fft_tile.cuh")),
             "plan_us_once": t_plan * 1e6}
-    if fft_ok:
+    stage_name = "image_stage_kernel<256, 3600, 16, 15, 15>"       # range tiles of scan s + rows of scan s-1
+    if pipelined:
+        # steady-state duration of one full stage launch: the marginal time of 8 more scans in one call
+        def call_ms(n, reps_=64):
+            m_, _ = graph_loop(torch, lambda i: scans_call(n), reps_, 3, 1, stream, world, device)
+            return m_ / reps_
+        t_stage = (call_ms(N_BUF) - call_ms(N_BUF // 2)) / (N_BUF - N_BUF // 2) * 1e-3
+        st_bytes = k1_bytes + k2f_bytes                               # raw in, S out | S in, H in, image out
+        kernels[stage_name] = {
+            "us_per_launch": t_stage * 1e6, "algorithmic_bytes": st_bytes, "gbs": st_bytes / t_stage / 1e9,
+            "hbm_frac": st_bytes / t_stage / 1e9 / hbm,
+            "traffic": recorded_traffic("image_stage_kernel<256,3600>", "indoor",
+                                        source_hash("image_pipeline.cu", "row_fft.cuh", "fft_tile.cuh")),
+            "note": "40 B/px: range compression of one scan (raw read, S write) and the azimuth filter of the "
+                    "previous one (S read, H read, image write) in one launch; S stays largely in L2, so DRAM "
+                    "traffic is below the algorithmic bytes"}
+    if pipelined:
+        dom = kernels[stage_name]
+        roofline = {"kernel": stage_name, "bound": "hbm", "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": dom["gbs"] / hbm, "traffic": dom["traffic"],
+                    "peak_note": f"HBM copy bandwidth of {peak_src} peaks",
+                    "algorithmic_bytes": dom["algorithmic_bytes"], "us_per_launch": dom["us_per_launch"]}
+    elif fft_ok:
         dom_name = fft_name if t_k2f >= t_k1 else "range_compress_kernel<256>"
         dom = kernels[dom_name]
         roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s",
@@ -507,7 +552,13 @@ def run_ours(args):
     paths = {"image_fft_px_s": value if fft_ok else None, "image_gather_px_s": world * px / t_gather_img,
              "image_migrating_px_s": world * px / t_mig_img,
              "timed_path": "rosar_image_fft" if fft_ok else "rosar_image", "autotune": choice}
-
+    if fft_ok:
+        # the per-scan call (rosar_image_fft, 2 launches per scan) on the same buffers
+        m, _ = graph_loop(torch, lambda i: image_step(i % N_BUF), max(512, args.steps // 4), 16, N_BUF, stream, world,
+                          device)
+        paths["image_fft_px_s"] = world * px / (m / max(512, args.steps // 4) * 1e-3)
+        paths["image_fft_scans_px_s"] = value if pipelined else None
+        paths["timed_path"] = "rosar_image_fft_scans" if pipelined else "rosar_image_fft"
     # end to end through the public API with pinned host buffers: rosar_image_fft_host enqueues the H2D copy
     # of the raw cube, the two kernels and the D2H copy of the image on its stream; consecutive steps go to
     # N_E2E streams with their own buffers, so one step's copies overlap the neighbours' compute
@@ -681,16 +732,22 @@ def run_ours(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "indoor scan: 3600 pulses x 256 ADC samples, K=64 of M=600, "
                                    "256x3600 polar image, complex64",
-                       "step": ("rosar_image_fft" if fft_ok else "rosar_image") +
-                               " = range compression + sparse azimuth filter, one scan; the weight design "
+                       "step": ("one scan of a rosar_image_fft_scans call over the resident scans "
+                                "(launch s runs the azimuth filter of scan s-1 with the range compression of "
+                                "scan s)" if pipelined else
+                                ("rosar_image_fft" if fft_ok else "rosar_image") + " call, one scan") +
+                               ": range compression + sparse azimuth filter; the weight design "
                                "(w, o and its frequency-domain plan H) is resident and reused",
                        "l2": f"inputs larger than L2: {N_BUF} rotating scan buffers "
                              f"({N_BUF * 3 * px * 8 / 2**20:.0f} MiB)",
-                       "launch": f"timed steps replay a CUDA graph of {N_BUF} captured steps (one per buffer): "
-                                 "2 kernels per step, no host work between steps",
+                       "launch": (f"timed steps replay a CUDA graph of one {N_BUF}-scan call ({N_BUF + 1} "
+                                  "launches chained by programmatic dependent launch), no host work between calls"
+                                  if pipelined else
+                                  f"timed steps replay a CUDA graph of {N_BUF} captured steps (one per buffer): "
+                                  "2 kernels per step, no host work between steps"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "clocks": clk.summary(),
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches,
             "roofline": roofline,
             "kernels": kernels,
             "paths": paths,

@@ -259,6 +259,26 @@ ROSAR_API rosar_status rosar_sparse_azimuth_fft(const rosar_c32 *S, const rosar_
 ROSAR_API rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int n_az, int L,
                                        rosar_c32 *workspace, rosar_c32 *out, void *stream);
 
+/*
+ * rosar_image_fft for a sequence of n_scans scans that share win and H (Eq. (38) then
+ * Eq. (43) per scan, Sec. III-D): out[s] equals rosar_image_fft(raw[s]) bit for bit.
+ * Where a pipelined plan exists for (L, n_az) (rosar_image_fft_scans_pipelined), the
+ * launches overlap consecutive scans: one launch runs the azimuth rows of scan s-1 together
+ * with the range compression of scan s, the two scans alternating between the halves of
+ * the workspace; otherwise the scans run one after the other through rosar_image_fft.
+ *   raw       [n_scans][n_az][L] complex, pulse-major (in)
+ *   win, H    as rosar_image_fft (in)
+ *   workspace [2][L][n_az] complex (scratch)
+ *   out       [n_scans][L][n_az] complex (out)
+ * Limits as rosar_image_fft; n_scans >= 1.  No argument may overlap another (except
+ * win/H, which are read only).  Errors as rosar_image_fft.
+ */
+ROSAR_API rosar_status rosar_image_fft_scans(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int n_scans,
+                                             int n_az, int L, rosar_c32 *workspace, rosar_c32 *out, void *stream);
+
+/* 1 if rosar_image_fft_scans overlaps consecutive scans for this (L, n_az), else 0. */
+ROSAR_API int rosar_image_fft_scans_pipelined(int L, int n_az);
+
 /* ------------------------------------------------------------------------
  * Differentiable form: a stack of n_scans scans [n_scans][n_rng][n_az] that share
  * one weight set, a per-pulse phase correction eps [n_scans][n_az] applied to the

@@ -63,6 +63,8 @@ _PROTOS = {
     "rosar_azimuth_plan": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_fft": (_I, [_P, _P, _I, _I, _P, _P]),
     "rosar_image_fft": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "rosar_image_fft_scans": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "rosar_image_fft_scans_pipelined": (_I, [_I, _I]),
     "rosar_phase_apply": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_scans": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),

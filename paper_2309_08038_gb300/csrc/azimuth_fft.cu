@@ -104,22 +104,12 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
 // the first inverse pass run as one step (row_filter_fused): four barriers for 16.15.15.
 template <int T, int N, int... R>
 __global__ void __launch_bounds__(T, (T <= 256 ? 2 : 1))
-azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, Layout lay, RowMap map,
+azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, RowMap map,
                          float2 *__restrict__ out) {
     extern __shared__ float2 sm[];
-    float2 *x = sm;
-    float2 *hb = x + padded_len(N);
-    float2 *tw = hb + padded_len(N);
     const size_t row = (size_t)blockIdx.x * N;
     const size_t hrow = (size_t)(blockIdx.x % map.h_rows) * N;
-    for (int n = threadIdx.x; n < N; n += T) cp_async8(hb + n, H + hrow + n);
-    cp_async_commit();
-    const float2 *tc, *tf;
-    build_twiddles(N, false, tw, &tc, &tf);
-    cp_async_wait<0>();
-    __syncthreads();
-    griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
-    row_filter_fused<N, T, true, R...>(S + row, hb, map.conj_h ? -1.f : 1.f, x, out + row, tc, tf);
+    filter_row_cta<T, N, R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm);
 }
 
 template <int MAXT>
@@ -259,19 +249,20 @@ bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, RowMap
         if (pl.rad[i] != rad[i]) return false;
     static int done[kMaxDevices] = {};
     const void *k = (const void *)azimuth_fft_fixed_kernel<T, N, R...>;
-    *st = ensure_smem(k, lay.bytes, done, "azimuth_fft");
+    constexpr size_t smem = filter_row_smem<N>();
+    *st = ensure_smem(k, smem, done, "azimuth_fft");
     if (*st != ROSAR_OK) return true;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_rng);
     cfg.blockDim = dim3(T);
-    cfg.dynamicSmemBytes = lay.bytes;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = ov ? 1 : 0;
-    *le = cudaLaunchKernelEx(&cfg, azimuth_fft_fixed_kernel<T, N, R...>, S, H, lay, map, out);
+    *le = cudaLaunchKernelEx(&cfg, azimuth_fft_fixed_kernel<T, N, R...>, S, H, map, out);
     *st = check_launch("azimuth_fft");
     return true;
 }

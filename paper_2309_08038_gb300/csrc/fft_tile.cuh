@@ -182,10 +182,12 @@ __device__ __forceinline__ void stockham_pass(float2 (&v)[Tile<L, P>::RM], int t
 // Range compression of pulses n0 .. n0+P-1 (those < n_az) into S[:, n0 .. n0+P), run by
 // blockDim.x == T*P threads with `smem` holding Tile<L, P>::SMEM_ELEMS elements.
 // build_tab = false reuses a twiddle table left in smem by a previous tile of the same L.
+// wait_before_store: a programmatic grid-dependency wait precedes the store of S (the previous kernel in the
+// stream may still read the buffer S is written to; raw is not written by it).
 template <int L, int P>
 __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const float *__restrict__ win, int n_az,
                                            bool centred, float2 *__restrict__ S, int n0, float2 *smem, bool build_tab,
-                                           bool vec_store) {
+                                           bool vec_store, bool wait_before_store = false) {
     using PL = Tile<L, P>;
     constexpr int RM = PL::RM, T = PL::T;
     float2 *tab = smem;               // two-level table of exp(-j*pi*q/L), q < 2L
@@ -223,6 +225,7 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
     // the transform is done: a kernel that depends on S (launched for programmatic overlap) may start
     // its own prologue now; it waits for this grid's completion before reading S.
     griddep_launch_dependents();
+    if (wait_before_store) griddep_wait();
     // coalesced store of the transposed tile: row l holds pulses n0..n0+P-1
     const int np = min(P, n_az - n0);
     if (vec_store && np == P) {

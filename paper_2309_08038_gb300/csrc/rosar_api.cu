@@ -298,6 +298,43 @@ rosar_status rosar_image_fft(const rosar_c32 *raw, const float *win, const rosar
                               n_az, reinterpret_cast<float2 *>(out), s, true);
 }
 
+int rosar_image_fft_scans_pipelined(int L, int n_az) {
+    return (is_pow2(L) && L >= 8 && L <= 4096 && n_az >= 1) ? image_pipeline_supported(L, n_az) : 0;
+}
+
+rosar_status rosar_image_fft_scans(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int n_scans, int n_az,
+                                   int L, rosar_c32 *workspace, rosar_c32 *out, void *stream) {
+    clear_error();
+    if (n_scans < 1) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_scans: n_scans=%d < 1", n_scans);
+    rosar_status st = check_range_args(raw, win, n_az, L, workspace);
+    if (st != ROSAR_OK) return st;
+    if (!H || !out) return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_scans: null H or out");
+    if (misaligned(H, 8) || misaligned(out, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_scans: misaligned pointer");
+    const size_t cube = sizeof(rosar_c32) * (size_t)n_az * L;
+    const size_t all = cube * (size_t)n_scans;
+    if (overlaps(raw, all, workspace, 2 * cube) || overlaps(out, all, raw, all) || overlaps(out, all, workspace, 2 * cube) ||
+        overlaps(out, all, H, cube) || overlaps(workspace, 2 * cube, H, cube))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_fft_scans: buffers overlap");
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "image_fft_scans: n_az=%d is not 2^a 3^b 5^c <= 16384", n_az);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (image_pipeline_supported(L, n_az))
+        return launch_image_pipeline(reinterpret_cast<const float2 *>(raw), win, reinterpret_cast<const float2 *>(H),
+                                     n_scans, n_az, L, reinterpret_cast<float2 *>(workspace),
+                                     reinterpret_cast<float2 *>(out), s);
+    const size_t elems = (size_t)n_az * L;
+    for (int i = 0; i < n_scans; ++i) {
+        st = launch_range_compress(reinterpret_cast<const float2 *>(raw + i * elems), win, n_az, L, 1,
+                                   reinterpret_cast<float2 *>(workspace), s);
+        if (st != ROSAR_OK) return st;
+        st = launch_azimuth_fft(reinterpret_cast<const float2 *>(workspace), reinterpret_cast<const float2 *>(H), L,
+                                n_az, reinterpret_cast<float2 *>(out + i * elems), s, true);
+        if (st != ROSAR_OK) return st;
+    }
+    return ROSAR_OK;
+}
+
 rosar_status rosar_image_fft_host(const rosar_c32 *raw_host, const float *win, const rosar_c32 *H, int n_az, int L,
                                   rosar_c32 *raw_dev, rosar_c32 *workspace, rosar_c32 *out_dev, rosar_c32 *out_host,
                                   void *stream) {

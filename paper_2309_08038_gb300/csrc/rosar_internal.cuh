@@ -85,6 +85,11 @@ rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, in
 
 // Azimuth filter in the frequency domain (azimuth_fft.cu).
 int azimuth_fft_supported(int n_az);
+
+// Pipelined multi-scan imaging (image_pipeline.cu): 1 if a stage kernel exists for (L, n_az).
+int image_pipeline_supported(int L, int n_az);
+rosar_status launch_image_pipeline(const float2 *raw, const float *win, const float2 *H, int n_scans, int n_az, int L,
+                                   float2 *workspace, float2 *out, cudaStream_t s);
 // overlap_predecessor: launch with programmatic stream serialization (only when the preceding kernel in
 // the stream writes S and nothing else the kernel reads before its grid-dependency wait, i.e. H).
 // h_rows: row b of S uses row (b mod h_rows) of H (0 = n_rng: one plan row per S row); conj_h: filter with conj(H),

@@ -295,8 +295,9 @@ __device__ __forceinline__ void dit_seq(float2 *x, const float2 *tc, const float
 // the same arithmetic (the two fused passes act on blocks of one butterfly, whose twiddles are 1).
 
 // First DIF pass (M = N, stride s = N/R) with its inputs read from global memory (ld.cg: src may have been
-// written earlier by the same kernel).
-template <int N, int R, int T>
+// written earlier by the same kernel).  WAIT_ASYNC: the thread's cp.async copies (the H row) complete before
+// the closing barrier, so they are visible to the whole CTA after it.
+template <int N, int R, int T, bool WAIT_ASYNC>
 __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src, float2 *x, const float2 *tc,
                                                  const float2 *tf) {
     constexpr int s = N / R;
@@ -312,6 +313,7 @@ __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src,
 #pragma unroll
         for (int q = 1; q < R; ++q) x[j + q * s] = cmul(v[q], wq[q]);
     }
+    if (WAIT_ASYNC) cp_async_wait<0>();
     __syncthreads();
 }
 
@@ -373,12 +375,13 @@ __device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float 
 }
 
 // src, dst: the row in global memory (natural order); x: N elements of shared memory (no padding); the
-// caller has built the twiddle table and synchronised.  No barrier at the end.
+// caller has built the twiddle table and synchronised.  With H_SMEM, h may still be arriving by cp.async
+// when this starts (waited for at the end of the first pass).  No barrier at the end.
 template <int N, int T, bool H_SMEM, int R1, int... Rs>
 __device__ __forceinline__ void row_filter_fused(const float2 *__restrict__ src, const float2 *h, float hs, float2 *x,
                                                  float2 *__restrict__ dst, const float2 *tc, const float2 *tf) {
     static_assert(sizeof...(Rs) >= 1, "at least two passes");
-    dif_first_global<N, R1, T>(src, x, tc, tf);
+    dif_first_global<N, R1, T, H_SMEM>(src, x, tc, tf);
     filter_middle<N, N / R1, T, H_SMEM, Rs...>(x, h, hs, tc, tf);
     dit_last_global<N, R1, T>(x, dst, tc, tf);
 }
@@ -439,6 +442,28 @@ __device__ __forceinline__ void build_twiddles(int N, bool full, float2 *tw, con
     *tf = tw;
 }
 
+
+// One row of the azimuth filter on one CTA of T threads with a compile-time plan (N with an odd factor):
+// stage the H row (cp.async) and the twiddle table, wait for the predecessor grid (S is complete), run
+// row_filter_fused.  sm: 2 (N + 1) + 64 + coarse_len(N) float2 of shared memory (filter_row_smem).
+template <int N>
+constexpr size_t filter_row_smem() { return sizeof(float2) * (size_t)(2 * padded_len(N) + 64 + coarse_len(N)); }
+
+template <int T, int N, int... R>
+__device__ __forceinline__ void filter_row_cta(const float2 *__restrict__ S_row, const float2 *__restrict__ H_row,
+                                               bool conj_h, float2 *__restrict__ out_row, float2 *sm) {
+    static_assert(pad_shift_for(N) == 31, "compile-time filter plans are for rows with an odd factor");
+    float2 *x = sm;
+    float2 *hb = x + padded_len(N);
+    float2 *tw = hb + padded_len(N);
+    for (int n = threadIdx.x; n < N; n += T) cp_async8(hb + n, H_row + n);   // waited for after the first pass
+    cp_async_commit();
+    const float2 *tc, *tf;
+    build_twiddles(N, false, tw, &tc, &tf);
+    __syncthreads();
+    griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
+    row_filter_fused<N, T, true, R...>(S_row, hb, conj_h ? -1.f : 1.f, x, out_row, tc, tf);
+}
 
 inline int threads_for(int N) { return N <= 4096 ? 256 : N <= 8192 ? 512 : 1024; }
 

@@ -251,6 +251,31 @@ def image_fft(raw, win, H, workspace=None, out=None, stream=None):
     return out
 
 
+def image_fft_scans(raw, win, H, workspace=None, out=None, stream=None):
+    """rosar_image_fft_scans: rosar_image_fft of every scan of raw [n_scans, n_az, L] with one plan H [L, n_az],
+    consecutive scans overlapped where a pipelined plan exists; workspace [2, L, n_az], out [n_scans, L, n_az]."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=3)
+    n_scans, n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(H, torch.complex64, "H", shape=(L, n_az))
+    if workspace is None:
+        workspace = torch.empty((2, L, n_az), dtype=torch.complex64, device=raw.device)
+    if out is None:
+        out = torch.empty((n_scans, L, n_az), dtype=torch.complex64, device=raw.device)
+    require(workspace, torch.complex64, "workspace", shape=(2, L, n_az))
+    require(out, torch.complex64, "out", shape=(n_scans, L, n_az))
+    check(lib.rosar_image_fft_scans(ptr(raw), ptr(win), ptr(H), n_scans, n_az, L, ptr(workspace), ptr(out),
+                                    stream_handle(stream)))
+    return out
+
+
+def image_fft_scans_pipelined(L, n_az):
+    """rosar_image_fft_scans_pipelined: True if image_fft_scans overlaps consecutive scans for (L, n_az)."""
+    return bool(_lib.load().rosar_image_fft_scans_pipelined(int(L), int(n_az)))
+
+
 # ------------------------------------------------------------------ differentiable form --
 
 def _stack(S, name):

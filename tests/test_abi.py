@@ -112,6 +112,28 @@ def test_image_fft_host_rejects_bad_arguments(lib):
     assert f(hr, None, FAKE2, 360, 64, FAKE, ws, od, hr, None) == 1            # host buffers alias
 
 
+def test_image_fft_scans_rejects_bad_arguments(lib):
+    f = lib.rosar_image_fft_scans
+    raw, ws, out = ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x40000000), ctypes.c_void_p(0x48000000)
+    assert f(raw, None, FAKE2, 0, 360, 64, ws, out, None) == 1                # no scans
+    assert f(raw, None, None, 2, 360, 64, ws, out, None) == 1                 # no plan
+    assert f(raw, None, FAKE2, 2, 360, 48, ws, out, None) == 2                # L not a power of two
+    assert f(raw, None, FAKE2, 2, 7 * 360, 64, ws, out, None) == 2            # n_az has a factor 7
+    cube = 360 * 64 * 8
+    assert f(raw, None, FAKE2, 2, 360, 64, ctypes.c_void_p(0x10000000 + cube), out, None) == 1   # ws inside raw[1]
+    assert f(raw, None, FAKE2, 2, 360, 64, ws, ctypes.c_void_p(0x40000000 + cube), None) == 1    # out inside ws[1]
+
+
+def test_pipelined_plans_are_the_planner_radices(lib):
+    """The multi-scan pipeline covers the compile-time (L, n_az) pairs whose azimuth radices match the
+    run-time planner; other shapes fall back to one scan after another (host-side query, no launch)."""
+    f = lib.rosar_image_fft_scans_pipelined
+    for L, n_az in [(64, 360), (128, 1800), (256, 1800), (128, 3600), (256, 3600), (512, 3600)]:
+        assert f(L, n_az) == 1, (L, n_az)
+    for L, n_az in [(256, 7200), (64, 3600), (1024, 14400), (48, 360), (256, 0)]:
+        assert f(L, n_az) == 0, (L, n_az)
+
+
 def test_image_rejects_bad_arguments(lib):
     f = lib.rosar_image
     assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2
