@@ -375,11 +375,11 @@ def run_reference(args):
         return
     t0 = time.perf_counter()
     steps = max(1, min(args.steps, 3))
-    warm = 1 if args.warmup > 0 else 0
+    warm = max(0, min(args.warmup, 3))            # warm-up steps: one image each
     vals = []
     cb = None
     for i in range(warm + steps):
-        cb = cpu_baseline_subprocess()
+        cb = cpu_baseline_subprocess(CPU_MIN_SECONDS if i >= warm else 0.0)
         if cb is None:
             print(json.dumps({"impl": "reference", "unavailable": "the oracle's CPU run failed"}))
             return
@@ -393,7 +393,8 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "indoor scan: 3600 pulses x 256 ADC samples, K=64 of M=600, "
                                   "256x3600 polar image, complex64",
-                      "steps_note": f"steps capped at {steps} (each >= {CPU_MIN_SECONDS:.0f} s of oracle work)"},
+                      "steps_note": f"steps capped at {steps} (each >= {CPU_MIN_SECONDS:.0f} s of oracle work); "
+                                    f"{warm} warm-up steps of one image each"},
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": time.perf_counter() - t0}
