@@ -386,7 +386,8 @@ typedef struct rosar_scan {
 typedef struct rosar_batch_tuning {
     int az_tile;            /* azimuth outputs per tile: 256, 512, 1024 or 2048; 0 selects 1024 */
     int ctas_per_sm;        /* persistent CTAs per SM; 0 or more than fit selects the occupancy limit */
-    int interleave;         /* 0: every range tile first, then every azimuth tile; 1: scan by scan */
+    int interleave;         /* 0: every range tile first, then every azimuth tile; 1: scan by scan;
+                               d in [2, 8]: range tiles run d-1 scans ahead of azimuth tiles */
     int spin_limit;         /* polls (~0.1 us apart) before a dependency wait gives up; 0 selects 2^24 */
     int debug_unmet_scan;   /* test hook, -1 = off: scan whose azimuth tiles wait for one range tile
                                more than exists, so that their wait must time out */

@@ -105,7 +105,7 @@ def batch_candidates():
     out = []
     for az_tile in (512, 1024, 2048):
         for ctas in (0, 2):
-            for interleave in (0, 1):
+            for interleave in (0, 1, 2, 3):
                 out.append(Tuning(az_tile=az_tile, ctas_per_sm=ctas, interleave=interleave))
     return out
 

@@ -14,7 +14,8 @@ from ._lib import check, require, stream_handle
 @dataclass
 class Tuning:
     """Mirrors rosar_batch_tuning.  az_tile in {256, 512, 1024, 2048}; ctas_per_sm 0 = occupancy limit;
-    interleave 0 = all range tiles first, 1 = scan by scan; spin_limit 0 = default."""
+    interleave 0 = all range tiles first, 1 = scan by scan, d >= 2 = range tiles d-1 scans ahead of the azimuth
+    tiles; spin_limit 0 = default."""
 
     az_tile: int = 1024
     ctas_per_sm: int = 0

@@ -266,6 +266,8 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
     if (tuning) tn = *tuning;
     if (tn.az_tile == 0) tn.az_tile = 1024;
     if (tn.spin_limit <= 0) tn.spin_limit = 1 << 24;
+    if (tn.interleave < 0 || tn.interleave > 8)
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: interleave=%d not in [0, 8]", tn.interleave);
     const int J = tn.az_tile / az::THREADS;
     if (tn.az_tile % az::THREADS || (J != 1 && J != 2 && J != 4 && J != 8))
         return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: az_tile=%d not in {256, 512, 1024, 2048}", tn.az_tile);
@@ -336,26 +338,30 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
         free(hg);
         return st;
     }
-    // ticket order
+    // ticket order.  Azimuth tiles of a scan always come after all of its range tiles, so every range tile an
+    // azimuth tile waits for has been handed to a running CTA (which waits on nothing) before it.
     int first = 0, ns = 0;
-    if (tn.interleave) {
+    auto range_seg = [&](int s) {
+        hg[ns++] = {first, s, 0, hs[s].range_tiles};
+        first += hs[s].range_tiles;
+    };
+    auto az_seg = [&](int s) {
+        const int na = hs[s].az_tiles_per_row * hs[s].L;
+        hg[ns++] = {first, s, 1, na};
+        first += na;
+    };
+    if (tn.interleave >= 1) {
+        // range tiles run (interleave - 1) scans ahead of the azimuth tiles: 1 = scan by scan, 2 = the next
+        // scan's range tiles before this scan's azimuth tiles (its S is produced while this one is filtered)
+        const int ahead = tn.interleave - 1;
+        for (int s = 0; s < n_scans && s < ahead; ++s) range_seg(s);
         for (int s = 0; s < n_scans; ++s) {
-            hg[ns++] = {first, s, 0, hs[s].range_tiles};
-            first += hs[s].range_tiles;
-            const int na = hs[s].az_tiles_per_row * hs[s].L;
-            hg[ns++] = {first, s, 1, na};
-            first += na;
+            if (s + ahead < n_scans) range_seg(s + ahead);
+            az_seg(s);
         }
     } else {
-        for (int s = 0; s < n_scans; ++s) {
-            hg[ns++] = {first, s, 0, hs[s].range_tiles};
-            first += hs[s].range_tiles;
-        }
-        for (int s = 0; s < n_scans; ++s) {
-            const int na = hs[s].az_tiles_per_row * hs[s].L;
-            hg[ns++] = {first, s, 1, na};
-            first += na;
-        }
+        for (int s = 0; s < n_scans; ++s) range_seg(s);
+        for (int s = 0; s < n_scans; ++s) az_seg(s);
     }
     const int total = first;
 

@@ -168,4 +168,7 @@ def test_batch_create_rejects_bad_arguments(lib):
     scans[0].o = 0x30000
     t = L.BatchTuningStruct(300, 0, 0, 0, -1)
     assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1   # az_tile
+    for il in (-1, 9):
+        t = L.BatchTuningStruct(1024, 0, il, 0, -1)
+        assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1   # interleave
     assert h.value is None

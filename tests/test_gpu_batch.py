@@ -81,7 +81,8 @@ def test_batch_equals_per_scan_image_and_oracle(rosar):
     b.close()
 
 
-@pytest.mark.parametrize("az_tile,interleave,ctas", [(256, 0, 0), (512, 1, 0), (2048, 0, 1), (1024, 1, 2)])
+@pytest.mark.parametrize("az_tile,interleave,ctas", [(256, 0, 0), (512, 1, 0), (2048, 0, 1), (1024, 1, 2),
+                                                      (1024, 2, 0), (512, 3, 1), (1024, 8, 0)])
 def test_every_tuning_gives_the_same_bits(rosar, az_tile, interleave, ctas):
     import torch
     scans, _ = _make_scans(torch, seed=1)
