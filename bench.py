@@ -215,6 +215,41 @@ def attach_plans(rosar, scans):
             sc["H"] = rosar.azimuth_plan(sc["w"], sc["o"], n_az)
 
 
+def highres_bench(torch, rosar, device, world, hbm):
+    """The high-resolution scan (14400 pulses x 1024 samples, per-row weights K=128 of M=2400): one
+    rosar_image_fft call per scan on 2 rotating scans of seeded random data (118 MB each), and its two
+    kernels alone; a parity case elsewhere, timed here for the record."""
+    import numpy as np
+    import synth
+    cfg = synth.HIGHRES
+    px = cfg.L * cfg.n_az
+    rng = np.random.default_rng(79)
+    raws = [torch.from_numpy((rng.standard_normal((cfg.n_az, cfg.L), dtype=np.float32) +
+                              1j * rng.standard_normal((cfg.n_az, cfg.L), dtype=np.float32)).astype(np.complex64)).to(device)
+            for _ in range(2)]
+    o = synth.draw_offsets(cfg)
+    w = torch.from_numpy(synth.default_weights(cfg, o)).to(device)
+    H = rosar.azimuth_plan(w, torch.from_numpy(o).to(device), cfg.n_az)
+    win = torch.from_numpy(synth.hann_window(cfg.L)).to(device)
+    S = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(2)]
+    out = [torch.empty((cfg.L, cfg.n_az), dtype=torch.complex64, device=device) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    n = 40
+
+    def per_call(fn):
+        m, _ = graph_loop(torch, fn, n, 4, 2, stream, world, device)
+        return m / n * 1e-3
+    t_img = per_call(lambda i: rosar.image_fft(raws[i % 2], win, H, workspace=S[i % 2], out=out[i % 2]))
+    t_k1 = per_call(lambda i: rosar.range_compress(raws[i % 2], win, out=S[i % 2]))
+    t_k2 = per_call(lambda i: rosar.sparse_azimuth_fft(S[i % 2], H, out=out[i % 2]))
+    del raws, S, out, H
+    return {"workload": "14400 pulses x 1024 samples, 1024 rows of K=128 taps (per-row weights), complex64",
+            "image_fft_px_s": world * px / t_img, "ms_per_image": t_img * 1e3,
+            "range_compress_kernel<1024>": {"us_per_launch": t_k1 * 1e6, "hbm_frac": 16.0 * px / t_k1 / 1e9 / hbm},
+            "azimuth_fft_fixed_kernel<1024, 14400, 8, 8, 15, 15>": {"us_per_launch": t_k2 * 1e6,
+                                                                      "hbm_frac": 24.0 * px / t_k2 / 1e9 / hbm}}
+
+
 def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_scans=16):
     """Differentiable form: 16 indoor-geometry scans with per-pulse phase errors N(0, 0.3 rad) on the raw
     cube; one step = images of the 16 scans, loss ||image - BPA image||^2 against the detached BPA image
@@ -669,6 +704,7 @@ def run_ours(args):
                     "8 flop per (pixel, tap, sample), run on the tensor cores (tcgen05, split bf16); paper_table lists the four methods of the paper's "
                     "processing-time tables on this workload (FFT+BPA nominal, FFT+SAS = the timed step)",
         }
+        compare["highres"] = highres_bench(torch, rosar, device, world, hbm)
 
     batched = {}
     if not args.no_batched:

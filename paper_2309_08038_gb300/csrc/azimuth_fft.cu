@@ -102,6 +102,11 @@ azimuth_fft_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, i
 // Compile-time plan for one row length (T threads, no padding: N has an odd factor, H staged): the first pass
 // reads S from global memory, the last writes the image, and the last forward pass, the product with H and
 // the first inverse pass run as one step (row_filter_fused): four barriers for 16.15.15.
+// Rows whose staged pair (S and H) would not fit the 200 KB shared-memory cap of the row layouts read H from
+// global memory in the fused step (14400-pulse rows).
+template <int N>
+constexpr bool stage_h_fits() { return filter_row_smem<N, true>() <= 200 * 1024; }
+
 template <int T, int N, int... R>
 __global__ void __launch_bounds__(T, (T <= 256 ? 2 : 1))
 azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict__ H, RowMap map,
@@ -109,7 +114,7 @@ azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict_
     extern __shared__ float2 sm[];
     const size_t row = (size_t)blockIdx.x * N;
     const size_t hrow = (size_t)(blockIdx.x % map.h_rows) * N;
-    filter_row_cta<T, N, R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm);
+    filter_row_cta<T, N, stage_h_fits<N>(), R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm);
 }
 
 template <int MAXT>
@@ -243,13 +248,13 @@ bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, RowMap
                const float2 *H, float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
     constexpr int rad[] = {R...};
     if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pad_shift_for(N) != 31 ||
-        !lay.stage_h || pl.npass != (int)sizeof...(R))
+        pl.npass != (int)sizeof...(R))
         return false;
     for (int i = 0; i < pl.npass; ++i)
         if (pl.rad[i] != rad[i]) return false;
     static int done[kMaxDevices] = {};
     const void *k = (const void *)azimuth_fft_fixed_kernel<T, N, R...>;
-    constexpr size_t smem = filter_row_smem<N>();
+    constexpr size_t smem = filter_row_smem<N, stage_h_fits<N>()>();
     *st = ensure_smem(k, smem, done, "azimuth_fft");
     if (*st != ROSAR_OK) return true;
     cudaLaunchConfig_t cfg = {};
@@ -284,6 +289,7 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
         if (try_fixed<256, 3600, 16, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
             try_fixed<256, 1800, 8, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
             try_fixed<512, 7200, 8, 4, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<1024, 14400, 8, 8, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
             try_fixed<256, 360, 8, 3, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst)) {
             if (fst == ROSAR_OK && fle != cudaSuccess)
                 return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(fle));

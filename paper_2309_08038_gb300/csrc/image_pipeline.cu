@@ -45,7 +45,7 @@ image_stage_kernel(const float2 *__restrict__ S_prev, const float2 *__restrict__
     griddep_launch_dependents();
     const int b = blockIdx.x;
     if (b < n_rows) {
-        rowfft::filter_row_cta<kStageThreads, N, R...>(S_prev + (size_t)b * N, H + (size_t)b * N, false,
+        rowfft::filter_row_cta<kStageThreads, N, true, R...>(S_prev + (size_t)b * N, H + (size_t)b * N, false,
                                                        out_prev + (size_t)b * N, sm);
     } else {
         constexpr int P = stage_pulses<L>();

@@ -444,25 +444,31 @@ __device__ __forceinline__ void build_twiddles(int N, bool full, float2 *tw, con
 
 
 // One row of the azimuth filter on one CTA of T threads with a compile-time plan (N with an odd factor):
-// stage the H row (cp.async) and the twiddle table, wait for the predecessor grid (S is complete), run
-// row_filter_fused.  sm: 2 (N + 1) + 64 + coarse_len(N) float2 of shared memory (filter_row_smem).
-template <int N>
-constexpr size_t filter_row_smem() { return sizeof(float2) * (size_t)(2 * padded_len(N) + 64 + coarse_len(N)); }
+// stage the H row (cp.async; H_SMEM) and the twiddle table, wait for the predecessor grid (S is complete), run
+// row_filter_fused.  sm: (H_SMEM ? 2 : 1) (N + 1) + 64 + coarse_len(N) float2 of shared memory
+// (filter_row_smem); without H_SMEM the fused middle step reads H from global memory (rows too long to
+// stage two of them).
+template <int N, bool H_SMEM = true>
+constexpr size_t filter_row_smem() {
+    return sizeof(float2) * (size_t)((H_SMEM ? 2 : 1) * padded_len(N) + 64 + coarse_len(N));
+}
 
-template <int T, int N, int... R>
+template <int T, int N, bool H_SMEM, int... R>
 __device__ __forceinline__ void filter_row_cta(const float2 *__restrict__ S_row, const float2 *__restrict__ H_row,
                                                bool conj_h, float2 *__restrict__ out_row, float2 *sm) {
     static_assert(pad_shift_for(N) == 31, "compile-time filter plans are for rows with an odd factor");
     float2 *x = sm;
     float2 *hb = x + padded_len(N);
-    float2 *tw = hb + padded_len(N);
-    for (int n = threadIdx.x; n < N; n += T) cp_async8(hb + n, H_row + n);   // waited for after the first pass
-    cp_async_commit();
+    float2 *tw = H_SMEM ? hb + padded_len(N) : hb;
+    if (H_SMEM) {
+        for (int n = threadIdx.x; n < N; n += T) cp_async8(hb + n, H_row + n);   // waited for after the first pass
+        cp_async_commit();
+    }
     const float2 *tc, *tf;
     build_twiddles(N, false, tw, &tc, &tf);
     __syncthreads();
     griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
-    row_filter_fused<N, T, true, R...>(S_row, hb, conj_h ? -1.f : 1.f, x, out_row, tc, tf);
+    row_filter_fused<N, T, H_SMEM, R...>(S_row, H_SMEM ? hb : H_row, conj_h ? -1.f : 1.f, x, out_row, tc, tf);
 }
 
 inline int threads_for(int N) { return N <= 4096 ? 256 : N <= 8192 ? 512 : 1024; }
