@@ -86,6 +86,11 @@ ROSAR_API int rosar_version(void);
 ROSAR_API rosar_status rosar_range_compress(const rosar_c32 *raw, const float *win, int n_az, int L,
                                   int centred, rosar_c32 *S, void *stream);
 
+/* rosar_range_compress of each scan of a stack in one launch:
+ *   raw [n_scans][n_az][L] (in), S [n_scans][L][n_az] (out); 1 <= n_scans <= 65535. */
+ROSAR_API rosar_status rosar_range_compress_scans(const rosar_c32 *raw, const float *win, int n_scans, int n_az,
+                                                  int L, int centred, rosar_c32 *S, void *stream);
+
 /*
  * Sparse-aperture azimuth matched filter, the FFT+SAS image of Sec. III-D,
  * Eq. (43) and Algorithm 2, with every tap of row r reading range bin r:
@@ -350,6 +355,11 @@ ROSAR_API rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *g
  */
 ROSAR_API rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, int n_az, int L,
                                                     int centred, rosar_c32 *grad_raw, void *stream);
+
+/* rosar_range_compress_adjoint of each scan of a stack in one launch:
+ *   g [n_scans][L][n_az] (in), grad_raw [n_scans][n_az][L] (out); 1 <= n_scans <= 65535. */
+ROSAR_API rosar_status rosar_range_compress_adjoint_scans(const rosar_c32 *g, const float *win, int n_scans, int n_az,
+                                                          int L, int centred, rosar_c32 *grad_raw, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched form: many scans of uneven n_az, L and K imaged by ONE persistent

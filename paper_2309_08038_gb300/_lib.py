@@ -48,6 +48,7 @@ _PROTOS = {
     "rosar_last_error": (ctypes.c_char_p, []),
     "rosar_version": (_I, []),
     "rosar_range_compress": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "rosar_range_compress_scans": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa": (_I, [_P, ctypes.POINTER(RadarStruct), _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_image": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
@@ -70,6 +71,7 @@ _PROTOS = {
     "rosar_sparse_azimuth_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_phase_grad": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_range_compress_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "rosar_range_compress_adjoint_scans": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_batch_workspace_bytes": (ctypes.c_size_t, [_I]),
     "rosar_batch_create": (_I, [ctypes.POINTER(ScanStruct), _I, ctypes.POINTER(BatchTuningStruct), _P,
                                 ctypes.c_size_t, ctypes.POINTER(_P)]),

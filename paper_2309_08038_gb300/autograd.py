@@ -79,5 +79,6 @@ def sparse_azimuth_phase(S, eps, w, o, method="auto"):
 
 
 def range_compress(raw, win=None, centred=True):
-    """Differentiable range compression of one scan, raw [n_az, L] -> S [L, n_az]."""
+    """Differentiable range compression of one scan, raw [n_az, L] -> S [L, n_az], or of a stack of scans,
+    raw [n_scans, n_az, L] -> S [n_scans, L, n_az] (one launch each way)."""
     return RangeCompress.apply(raw, win, centred)

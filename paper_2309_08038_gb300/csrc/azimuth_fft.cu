@@ -21,7 +21,11 @@
 // natural order.  Twiddles exp(-2*pi*i*q/N) come from a two-level shared table
 // (q >> 6, q & 63) built per CTA with sincospif.
 
+#include <cooperative_groups.h>
+
 #include "row_fft.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rosar {
 namespace {
@@ -190,6 +194,86 @@ azimuth_xspec_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St
     }
 }
 
+// Compile-time-plan form of the weight gradient: the scans of a row are split over a cluster of G CTAs
+// (rank c takes scans c, c + G, ...).  Each CTA transforms its rows with the first DIF pass read straight from
+// global memory and the last DIF pass of both rows fused with the accumulation P += X . conj(Y); rank 0 then
+// adds the other ranks' partial cross-spectra from distributed shared memory in rank order (deterministic),
+// runs the DIT sequence and samples the taps.  grid = (G, n_rng), cluster (G, 1, 1).
+template <int N, int M, int T, int R, int... Rest>
+__device__ __forceinline__ void xspec_tail(float2 *x, float2 *y, float2 *P, const float2 *tc, const float2 *tf) {
+    if constexpr (sizeof...(Rest) == 0) {
+        static_assert(M == R, "the last radix spans the last block");
+#pragma unroll 1
+        for (int b = threadIdx.x; b < N / R; b += T) {
+            float2 v[R], u[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                v[q] = x[b * R + q];
+                u[q] = y[b * R + q];
+            }
+            small_dft<R>(v);
+            small_dft<R>(u);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {             // P += X . conj(Y)
+                float2 &p = P[b * R + q];
+                p.x = fmaf(v[q].x, u[q].x, fmaf(v[q].y, u[q].y, p.x));
+                p.y = fmaf(v[q].y, u[q].x, fmaf(-v[q].x, u[q].y, p.y));
+            }
+        }
+        __syncthreads();
+    } else {
+        dif_pass_c<N, M, R, false, T>(x, tc, tf);
+        dif_pass_c<N, M, R, false, T>(y, tc, tf);
+        xspec_tail<N, M / R, T, Rest...>(x, y, P, tc, tf);
+    }
+}
+
+template <int T, int N, int R1, int... Rs>
+__global__ void __launch_bounds__(T, 2)
+azimuth_xspec_fixed_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St, const int32_t *__restrict__ o,
+                           int o_row_stride, int n_scans, int n_rng, int K, float2 *__restrict__ grad_w) {
+    extern __shared__ float2 sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int G = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int r = blockIdx.y;
+    float2 *P = sm;
+    float2 *x = P + padded_len(N);
+    float2 *y = x + padded_len(N);
+    float2 *tw = y + padded_len(N);
+    const float2 *tc, *tf;
+    build_twiddles(N, false, tw, &tc, &tf);
+    for (int n = threadIdx.x; n < N; n += T) P[n] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int sc = rank; sc < n_scans; sc += G) {
+        const size_t row = ((size_t)sc * n_rng + r) * N;
+        dif_first_global<N, R1, T, false>(g + row, x, tc, tf);
+        dif_first_global<N, R1, T, false>(St + row, y, tc, tf);
+        xspec_tail<N, N / R1, T, Rs...>(x, y, P, tc, tf);
+    }
+    cluster.sync();
+    if (rank == 0) {
+        for (int n = threadIdx.x; n < N; n += T) {
+            float2 acc = P[n];
+            for (int c = 1; c < G; ++c) {
+                const float2 v = cluster.map_shared_rank(P, c)[n];
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            P[n] = acc;
+        }
+    }
+    cluster.sync();                       // the other ranks' partial sums stay alive until rank 0 has read them
+    if (rank != 0) return;
+    dit_seq<N, N, false, T, R1, Rs...>(P, tc, tf);
+    const float inv_n = (float)(1.0 / (double)N);
+    const int32_t *orow = o + (size_t)r * o_row_stride;
+    for (int k = threadIdx.x; k < K; k += T) {
+        const int tau = pmod(__ldg(orow + k), N);
+        grad_w[(size_t)r * K + k] = cscale(P[tau], inv_n);
+    }
+}
+
 constexpr size_t AF_SMEM_CAP = 200 * 1024;
 
 Layout layout_for(int N, bool with_h) {
@@ -311,11 +395,61 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     return st;
 }
 
+namespace {
+
+// Launches the cluster-split weight gradient when n_az has this compile-time plan (the planner's radices);
+// returns false to fall back to one CTA per row.
+template <int T, int N, int... R>
+bool try_xspec_fixed(int n_az, const RowPlan &pl, const float2 *g, const float2 *S_t, const int32_t *o,
+                     int o_row_stride, int n_scans, int n_rng, int K, float2 *grad_w, cudaStream_t s,
+                     rosar_status *st) {
+    constexpr int rad[] = {R...};
+    if (n_az != N || threads_for(N) != T || pl.npass != (int)sizeof...(R) || n_rng > 65535) return false;
+    for (int i = 0; i < pl.npass; ++i)
+        if (pl.rad[i] != rad[i]) return false;
+    static int done[kMaxDevices] = {};
+    const void *k = (const void *)azimuth_xspec_fixed_kernel<T, N, R...>;
+    constexpr size_t smem = sizeof(float2) * (3 * (size_t)padded_len(N) + 64 + coarse_len(N));
+    *st = ensure_smem(k, smem, done, "weight_grad_fft");
+    if (*st != ROSAR_OK) return true;
+    // scans per CTA: about 4 (G = 4 at 16 scans), G a power of two <= 8 and <= n_scans
+    int G = 1;
+    while (G < 8 && 2 * G <= n_scans && 4 * G < n_scans) G *= 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G, n_rng);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = G;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, azimuth_xspec_fixed_kernel<T, N, R...>, g, S_t, o, o_row_stride,
+                                             n_scans, n_rng, K, grad_w);
+    *st = e != cudaSuccess ? set_error(ROSAR_ERR_CUDA, "weight_grad_fft: launch failed: %s", cudaGetErrorString(e))
+                           : check_launch("weight_grad_fft");
+    return true;
+}
+
+}  // namespace
+
 rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
                                             int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s) {
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
+    {
+        rosar_status st = ROSAR_OK;
+        if (try_xspec_fixed<256, 3600, 16, 15, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s,
+                                                   &st) ||
+            try_xspec_fixed<256, 1800, 8, 15, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s,
+                                                  &st) ||
+            try_xspec_fixed<256, 360, 8, 3, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s, &st))
+            return st;
+    }
     const size_t bytes = sizeof(float2) * (3 * (size_t)padded_len(n_az) + 64 + coarse_len(n_az));
     if (bytes > AF_SMEM_CAP)
         return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: n_az=%d needs %zu bytes of shared memory", n_az, bytes);

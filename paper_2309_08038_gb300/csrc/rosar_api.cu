@@ -119,6 +119,19 @@ rosar_status rosar_range_compress(const rosar_c32 *raw, const float *win, int n_
                                  reinterpret_cast<float2 *>(S), static_cast<cudaStream_t>(stream));
 }
 
+rosar_status rosar_range_compress_scans(const rosar_c32 *raw, const float *win, int n_scans, int n_az, int L,
+                                        int centred, rosar_c32 *S, void *stream) {
+    clear_error();
+    if (n_scans < 1 || n_scans > 65535)
+        return set_error(ROSAR_ERR_INVALID_ARG, "range_compress_scans: n_scans=%d not in [1, 65535]", n_scans);
+    rosar_status st = check_range_args(raw, win, n_az, L, S);
+    if (st != ROSAR_OK) return st;
+    const size_t all = sizeof(rosar_c32) * (size_t)n_az * L * n_scans;
+    if (overlaps(raw, all, S, all)) return set_error(ROSAR_ERR_INVALID_ARG, "range_compress_scans: raw and S overlap");
+    return launch_range_compress(reinterpret_cast<const float2 *>(raw), win, n_az, L, centred,
+                                 reinterpret_cast<float2 *>(S), static_cast<cudaStream_t>(stream), n_scans);
+}
+
 rosar_status rosar_sparse_azimuth(const rosar_c32 *S, const rosar_c32 *w, const int32_t *o, int o_row_stride,
                                   int n_rng, int n_az, int K, rosar_c32 *out, void *stream) {
     clear_error();
@@ -500,6 +513,21 @@ rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, 
     if (st != ROSAR_OK) return st;
     return launch_range_compress_adjoint(reinterpret_cast<const float2 *>(g), win, n_az, L, centred,
                                          reinterpret_cast<float2 *>(grad_raw), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_range_compress_adjoint_scans(const rosar_c32 *g, const float *win, int n_scans, int n_az, int L,
+                                                int centred, rosar_c32 *grad_raw, void *stream) {
+    clear_error();
+    if (n_scans < 1 || n_scans > 65535)
+        return set_error(ROSAR_ERR_INVALID_ARG, "range_compress_adjoint_scans: n_scans=%d not in [1, 65535]", n_scans);
+    rosar_status st = check_range_args(g, win, n_az, L, grad_raw);
+    if (st != ROSAR_OK) return st;
+    const size_t all = sizeof(rosar_c32) * (size_t)n_az * L * n_scans;
+    if (overlaps(g, all, grad_raw, all))
+        return set_error(ROSAR_ERR_INVALID_ARG, "range_compress_adjoint_scans: g and grad_raw overlap");
+    return launch_range_compress_adjoint(reinterpret_cast<const float2 *>(g), win, n_az, L, centred,
+                                         reinterpret_cast<float2 *>(grad_raw), static_cast<cudaStream_t>(stream),
+                                         n_scans);
 }
 
 // ------------------------------------------------------- range-migration-aware taps --

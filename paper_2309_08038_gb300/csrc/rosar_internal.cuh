@@ -58,7 +58,7 @@ __device__ __forceinline__ int pmod(int a, int n) {
 // Each .cu file exposes a host-side launcher; the API layer validates first.
 
 rosar_status launch_range_compress(const float2 *raw, const float *win, int n_az, int L, int centred,
-                                   float2 *S, cudaStream_t s);
+                                   float2 *S, cudaStream_t s, int n_scans = 1);
 
 rosar_status launch_sparse_azimuth(const float2 *S, const float2 *w, const int32_t *o, int o_row_stride,
                                    int n_rng, int n_az, int K, float2 *out, cudaStream_t s);
@@ -81,7 +81,7 @@ rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, cons
 rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *eps, int n_scans, int n_rng, int n_az,
                                float *grad_eps, float2 *grad_S, cudaStream_t s);
 rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, int n_az, int L, int centred,
-                                           float2 *grad_raw, cudaStream_t s);
+                                           float2 *grad_raw, cudaStream_t s, int n_scans = 1);
 
 // Azimuth filter in the frequency domain (azimuth_fft.cu).
 int azimuth_fft_supported(int n_az);

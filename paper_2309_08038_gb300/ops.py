@@ -37,16 +37,25 @@ class Radar:
 
 
 def range_compress(raw, win=None, centred=True, out=None, stream=None):
-    """rosar_range_compress: raw [n_az, L] complex64 -> S [L, n_az] complex64 (range-major)."""
+    """rosar_range_compress: raw [n_az, L] complex64 -> S [L, n_az] complex64 (range-major); a stack
+    raw [n_scans, n_az, L] -> S [n_scans, L, n_az] goes through rosar_range_compress_scans (one launch)."""
     lib = _lib.load()
-    require(raw, torch.complex64, "raw", ndim=2)
-    n_az, L = raw.shape
+    if not isinstance(raw, torch.Tensor) or raw.dim() not in (2, 3):
+        raise ValueError("raw must be a [n_az, L] or [n_scans, n_az, L] tensor")
+    require(raw, torch.complex64, "raw", ndim=raw.dim())
+    *lead, n_az, L = raw.shape
     if win is not None:
         require(win, torch.float32, "win", shape=(L,))
+    shape = (*lead, L, n_az)
     if out is None:
-        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
-    require(out, torch.complex64, "out", shape=(L, n_az))
-    check(lib.rosar_range_compress(ptr(raw), ptr(win), n_az, L, int(bool(centred)), ptr(out), stream_handle(stream)))
+        out = torch.empty(shape, dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=shape)
+    if lead:
+        check(lib.rosar_range_compress_scans(ptr(raw), ptr(win), lead[0], n_az, L, int(bool(centred)), ptr(out),
+                                             stream_handle(stream)))
+    else:
+        check(lib.rosar_range_compress(ptr(raw), ptr(win), n_az, L, int(bool(centred)), ptr(out),
+                                       stream_handle(stream)))
     return out
 
 
@@ -368,17 +377,25 @@ def phase_grad(S_t, grad_S_t, eps, want_eps=True, want_S=False, stream=None):
 
 
 def range_compress_adjoint(g, win=None, centred=True, out=None, stream=None):
-    """rosar_range_compress_adjoint: g [L, n_az] -> grad_raw [n_az, L]."""
+    """rosar_range_compress_adjoint: g [L, n_az] -> grad_raw [n_az, L]; a stack g [n_scans, L, n_az] ->
+    grad_raw [n_scans, n_az, L] goes through rosar_range_compress_adjoint_scans (one launch)."""
     lib = _lib.load()
-    require(g, torch.complex64, "g", ndim=2)
-    L, n_az = g.shape
+    if not isinstance(g, torch.Tensor) or g.dim() not in (2, 3):
+        raise ValueError("g must be a [L, n_az] or [n_scans, L, n_az] tensor")
+    require(g, torch.complex64, "g", ndim=g.dim())
+    *lead, L, n_az = g.shape
     if win is not None:
         require(win, torch.float32, "win", shape=(L,))
+    shape = (*lead, n_az, L)
     if out is None:
-        out = torch.empty((n_az, L), dtype=torch.complex64, device=g.device)
-    require(out, torch.complex64, "grad_raw", shape=(n_az, L))
-    check(lib.rosar_range_compress_adjoint(ptr(g), ptr(win), n_az, L, int(bool(centred)), ptr(out),
-                                           stream_handle(stream)))
+        out = torch.empty(shape, dtype=torch.complex64, device=g.device)
+    require(out, torch.complex64, "grad_raw", shape=shape)
+    if lead:
+        check(lib.rosar_range_compress_adjoint_scans(ptr(g), ptr(win), lead[0], n_az, L, int(bool(centred)),
+                                                     ptr(out), stream_handle(stream)))
+    else:
+        check(lib.rosar_range_compress_adjoint(ptr(g), ptr(win), n_az, L, int(bool(centred)), ptr(out),
+                                               stream_handle(stream)))
     return out
 
 

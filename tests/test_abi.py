@@ -134,6 +134,15 @@ def test_pipelined_plans_are_the_planner_radices(lib):
         assert f(L, n_az) == 0, (L, n_az)
 
 
+def test_stacked_range_calls_reject_bad_arguments(lib):
+    raw, S = ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x40000000)
+    for f in (lib.rosar_range_compress_scans, lib.rosar_range_compress_adjoint_scans):
+        assert f(raw, None, 0, 360, 64, 1, S, None) == 1                          # no scans
+        assert f(raw, None, 65536, 360, 64, 1, S, None) == 1                      # too many scans
+        assert f(raw, None, 2, 360, 48, 1, S, None) == 2                          # L not a power of two
+        assert f(raw, None, 2, 360, 64, 1, ctypes.c_void_p(0x10000000 + 360 * 64 * 8), None) == 1   # overlap
+
+
 def test_image_rejects_bad_arguments(lib):
     f = lib.rosar_image
     assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2

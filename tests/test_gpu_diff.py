@@ -84,6 +84,37 @@ def test_range_compress_adjoint_matches_oracle(rosar, L, n_az):
         assert _rel(got, O.range_compress_adjoint(g, win, centred)) < 2e-6, (L, n_az, centred)
 
 
+@pytest.mark.parametrize("L,n_az,n_scans", [(64, 360, 3), (256, 3600, 2), (16, 37, 5)])
+def test_stacked_range_calls_equal_per_scan_calls(rosar, L, n_az, n_scans):
+    """rosar_range_compress_scans / rosar_range_compress_adjoint_scans (one launch, grid.y = scan) give each scan
+    the bits of its own single-scan call, with and without centring."""
+    import torch
+    rng = np.random.default_rng(L + n_scans)
+    raw, g = _cuda(torch, _c(rng, n_scans, n_az, L)), _cuda(torch, _c(rng, n_scans, L, n_az))
+    win = _cuda(torch, synth.hann_window(L))
+    for centred in (True, False):
+        S = rosar.range_compress(raw, win, centred=centred)
+        gr = rosar.range_compress_adjoint(g, win, centred=centred)
+        for s in range(n_scans):
+            assert torch.equal(S[s], rosar.range_compress(raw[s], win, centred=centred)), (s, centred)
+            assert torch.equal(gr[s], rosar.range_compress_adjoint(g[s], win, centred=centred)), (s, centred)
+
+
+def test_range_compress_autograd_stack(rosar):
+    import torch
+    rng = np.random.default_rng(41)
+    n_scans, n_az, L = 3, 50, 64
+    raw = _c(rng, n_scans, n_az, L)
+    B = _c(rng, n_scans, L, n_az)
+    win = synth.hann_window(L)
+    t = _cuda(torch, raw).requires_grad_(True)
+    S = rosar.autograd.range_compress(t, _cuda(torch, win))
+    torch.sum(torch.abs(S - _cuda(torch, B)) ** 2).backward()
+    for s in range(n_scans):
+        ref = O.range_compress_adjoint(2.0 * (O.range_compress(raw[s], win) - B[s]), win)
+        assert _rel(t.grad[s].cpu().numpy(), ref) < 1e-5, s
+
+
 def _crop_problem(seed=3):
     """The 64-pulse crop: 64 pulses, 32 range rows, K = 16 taps of M = 32, two scans."""
     rng = np.random.default_rng(seed)
@@ -187,13 +218,15 @@ def test_full_diff_workload_against_oracle(rosar, method):
     assert _rel(gw, ref_w) < TOL_GRAD
 
 
-@pytest.mark.parametrize("n_az,per_row", [(48, False), (1000, True), (3600, False), (7200, True)])
-def test_frequency_domain_adjoints_match_oracle(rosar, n_az, per_row):
+@pytest.mark.parametrize("n_az,per_row,n_scans", [(48, False, 3), (1000, True, 3), (3600, False, 3), (7200, True, 3),
+                                                  (3600, False, 1), (3600, True, 9), (1800, True, 6), (360, False, 16)])
+def test_frequency_domain_adjoints_match_oracle(rosar, n_az, per_row, n_scans):
     """Stacked FFT filter (plan shared by the scans), its adjoint (conj of the plan) and the cross-spectrum
-    weight gradient against the oracle's filter and adjoints; shared and per-row offsets, wrapping offsets."""
+    weight gradient against the oracle's filter and adjoints; shared and per-row offsets, wrapping offsets.
+    360/1800/3600-pulse rows take the cluster-split weight gradient (1, 2 or 4 CTAs per row by scan count)."""
     import torch
-    rng = np.random.default_rng(n_az)
-    n_scans, n_rng, K = 3, 5, 12
+    rng = np.random.default_rng(n_az + n_scans)
+    n_rng, K = 5, 12
     M = min(n_az, 600)
     if per_row:
         o = np.stack([np.sort(rng.choice(M, K, replace=False)) - M // 2 for _ in range(n_rng)]).astype(np.int32)
