@@ -1,7 +1,9 @@
-// Mixed-radix row FFT used by the frequency-domain azimuth filter (azimuth_fft.cu) and by
-// the batched persistent kernel (batch.cu): in-place decimation-in-frequency forward
-// transform (digit-reversed output) and its transposed decimation-in-time sequence.
-// All functions run on the whole CTA (blockDim.x threads, any count) and end with a barrier.
+// Mixed-radix row FFT used by the frequency-domain azimuth filter (azimuth_fft.cu), the
+// pipelined multi-scan stage kernel (image_pipeline.cu) and the batched persistent kernel
+// (batch.cu): in-place decimation-in-frequency forward transform (digit-reversed output) and
+// its transposed decimation-in-time sequence, radices 16, 8, 4, 2, 5, 3 and a prime-factor 15.
+// The pass functions run on the whole CTA (blockDim.x threads, any count) and end with a barrier
+// (row_filter_fused and dit_last_global, whose last pass writes global memory, do not).
 #pragma once
 
 #include <map>
