@@ -105,7 +105,7 @@ constexpr int TILE = BT * KR * 2;            // bytes of one operand tile (A: 12
 constexpr int STAGE = 4 * TILE;              // A hi, A lo, B hi, B lo
 constexpr int AFS = MC + 4;                  // fp32 A staging row stride (160 B: 16-byte lane accesses spread banks)
 constexpr int AF = BT * AFS * 8;             // fp32 A staging of one stage (cp.async target): 20 KB
-constexpr int SMEM = 2 * STAGE + 2 * AF + 3 * BR * 16 + 64;
+constexpr int SMEM = 2 * STAGE + 2 * AF + 6 * BR * 16 + 64;   // + [3][BR] tap table and [3][BR] phasor steps
 constexpr int TMEM_COLS = 2 * NN;             // period accumulator X, running sum Y
 constexpr int PERIOD = 128;                  // stages per period: 768 MMA steps accumulate in X before X is added into Y
 constexpr long long SPIN_LIMIT = 1LL << 26;
@@ -188,7 +188,8 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
     float2 *af = reinterpret_cast<float2 *>(smem + 2 * STAGE);   // [2][BT][AFS] raw samples, one stage ahead
     float4 *tab = reinterpret_cast<float4 *>(smem + 2 * STAGE + 2 * AF);  // [3][BR]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 2 * AF + 3 * BR * 16);
+    float4 *stp = tab + 3 * BR;              // [3][BR]: exp(-j pi phi), exp(-j pi 16 phi) of the same (row, tap)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE + 2 * AF + 6 * BR * 16);
     uint64_t *full = bars, *empty = bars + 2, *fold_bar = bars + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 5);
 
@@ -232,6 +233,10 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             }
         }
         tab[(kk % 3) * BR + j] = t;
+        // fast-time phasor steps of one and of MC samples, from the exactly reduced phase (zero rows: 1)
+        const float4 u = make_float4(1.f, 0.f, t.z, t.w);
+        const float2 s1 = phasor_term(u, 1.f, 1.f), s16 = phasor_term(u, 1.f, (float)MC);
+        stp[(kk % 3) * BR + j] = make_float4(s1.x, s1.y, s16.x, s16.y);
     };
     if (warp < 2 && stages > 0) {
         build_tab(0);
@@ -285,6 +290,7 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             have_y = true;
         };
         if (stages > 0) prefetch_A(0);
+        float2 e_run = make_float2(1.f, 0.f);  // fast-time phasor at this thread's first sample of the stage
         for (int s = 0; s < stages; ++s) {
             const int b = s & 1;
             uint8_t *st = stage_base + b * STAGE;
@@ -321,12 +327,14 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             {
                 const int r = 8 * warp + (lane & 7), c = lane >> 3;
                 const float4 t4 = tab[(kk % 3) * BR + r];
+                const float4 st4 = stp[(kk % 3) * BR + r];
                 const int mb = m0 + 4 * c;
-                const float2 e0 = phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref);
-                float sn, cs;
-                sincospif(t4.z, &sn, &cs);
-                const float2 step = make_float2(cs, -sn);                    // exp(-j pi phi), one sample
-                float2 e = e0;
+                // the thread keeps the same (row, 4 samples) slot every stage: the phasor at its first sample is
+                // taken exactly at the tap's first stage and advanced by MC samples per stage after that
+                e_run = m0 == 0 ? phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref)
+                                : cmul(e_run, make_float2(st4.z, st4.w));
+                const float2 step = make_float2(st4.x, st4.y);               // exp(-j pi phi), one sample
+                float2 e = e_run;
                 uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
