@@ -597,6 +597,18 @@ def run_ours(args):
         paths["image_fft_px_s"] = world * px / (m / max(512, args.steps // 4) * 1e-3)
         paths["image_fft_scans_px_s"] = value if pipelined else None
         paths["timed_path"] = "rosar_image_fft_scans" if pipelined else "rosar_image_fft"
+        # the azimuth filter alone over the N_BUF range-compressed scans in one launch (N_BUF x 256 rows)
+        S_stack = rosar.range_compress(raw_stack, win)
+        n_f = 64
+        m, _ = graph_loop(torch, lambda i: rosar.sparse_azimuth_fft_scans(S_stack, H, out=out_stack), n_f, 3, 1,
+                          stream, world, device)
+        t_f = m / n_f * 1e-3
+        paths["filter_scans"] = {"scans": N_BUF, "us_per_scan": t_f / N_BUF * 1e6,
+                                 "px_s": world * px * N_BUF / t_f,
+                                 "hbm_frac_24B_per_px": 24.0 * px * N_BUF / t_f / 1e9 / hbm,
+                                 "note": "rosar_sparse_azimuth_fft_scans over the scans' S in one launch "
+                                         "(S, H and image: 24 B/px)"}
+        del S_stack
     # end to end through the public API with pinned host buffers: rosar_image_fft_host enqueues the H2D copy
     # of the raw cube, the two kernels and the D2H copy of the image on its stream; consecutive steps go to
     # N_E2E streams with their own buffers, so one step's copies overlap the neighbours' compute
