@@ -8,6 +8,14 @@
 namespace rosar {
 namespace fft {
 
+// A raw sample is read once: through L2 without allocating in L1, which stays with the window and the data the
+// other CTAs of the SM reuse.
+__device__ __forceinline__ float2 ld_stream(const float2 *p) {
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // exp(-2*pi*i*q/16) for compile-time q (after unrolling the switch folds away).
 __device__ __forceinline__ float2 w16(int q) {
     constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
@@ -203,7 +211,7 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
             const int m = t + r * T;
-            const float2 x = live ? __ldg(src + m) : make_float2(0.f, 0.f);
+            const float2 x = live ? ld_stream(src + m) : make_float2(0.f, 0.f);
             const float wm = win ? __ldg(win + m) : 1.f;
             v[r] = cscale(x, wm);
         }
