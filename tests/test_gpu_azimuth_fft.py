@@ -207,3 +207,29 @@ def test_image_fft_scans_matches_oracle_and_replays_in_a_graph(rosar):
             g.replay()
     side.synchronize()
     assert torch.equal(out, got)
+
+
+def test_image_fft_scans_full_size_in_the_benchmark_configuration(rosar):
+    """The benchmark's launch configuration: 16 indoor scans (3600 x 256, K = 64 of M = 600) in one
+    rosar_image_fft_scans call; sampled rows of the first, a middle and the last scan against the FP64 oracle
+    (range DFT of the sampled bins, then the sparse filter), each within 1e-4."""
+    import torch
+    cfg = synth.INDOOR
+    rng = np.random.default_rng(16)
+    n_scans = 16
+    raw = _c(rng, n_scans, cfg.n_az, cfg.L)
+    o = synth.draw_offsets(cfg)
+    w = synth.default_weights(cfg, o)
+    win = synth.hann_window(cfg.L)
+    H = rosar.azimuth_plan(torch.from_numpy(w).cuda(), torch.from_numpy(o).cuda(), cfg.n_az)
+    assert rosar.image_fft_scans_pipelined(cfg.L, cfg.n_az)
+    got = rosar.image_fft_scans(torch.from_numpy(raw).cuda(), torch.from_numpy(win).cuda(), H)
+    rows = [0, 1, 97, 255]
+    for s in (0, 7, 15):
+        ref = O.sparse_azimuth(O.range_compress(raw[s], win, bins=rows), w[rows], o)
+        g = got[s, rows].cpu().numpy()
+        for i, r in enumerate(rows):
+            if not np.any(ref[i]):              # the default weights of the rotation-circle row are zero
+                assert not np.any(g[i]), (s, r)
+            else:
+                assert _rel(g[i], ref[i]) < TOL_IMAGE, (s, r)
