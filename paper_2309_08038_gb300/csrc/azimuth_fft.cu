@@ -328,8 +328,8 @@ namespace {
 // Launches the compile-time-plan kernel when the run-time planner picks exactly its radices for n_az (so H,
 // made by the run-time plan, is in the same order); returns false to fall back to the run-time plan.
 template <int T, int N, int... R>
-bool try_fixed(int n_az, const RowPlan &pl, int n_rng, const Layout &lay, RowMap map, bool ov, const float2 *S,
-               const float2 *H, float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
+bool try_fixed(int n_az, const RowPlan &pl, int n_rng, RowMap map, bool ov, const float2 *S, const float2 *H,
+               float2 *out, cudaStream_t s, cudaError_t *le, rosar_status *st) {
     constexpr int rad[] = {R...};
     if (n_az != N || threads_for(N) != T || pl.pad_shift != pad_shift_for(N) || pad_shift_for(N) != 31 ||
         pl.npass != (int)sizeof...(R))
@@ -370,11 +370,11 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
     {
         cudaError_t fle = cudaSuccess;
         rosar_status fst = ROSAR_OK;
-        if (try_fixed<256, 3600, 16, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<256, 1800, 8, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<512, 7200, 8, 4, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<1024, 14400, 8, 8, 15, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst) ||
-            try_fixed<256, 360, 8, 3, 15>(n_az, pl, n_rng, lay, map, ov, S, H, out, s, &fle, &fst)) {
+        if (try_fixed<256, 3600, 16, 15, 15>(n_az, pl, n_rng, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<256, 1800, 8, 15, 15>(n_az, pl, n_rng, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<512, 7200, 8, 4, 15, 15>(n_az, pl, n_rng, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<1024, 14400, 8, 8, 15, 15>(n_az, pl, n_rng, map, ov, S, H, out, s, &fle, &fst) ||
+            try_fixed<256, 360, 8, 3, 15>(n_az, pl, n_rng, map, ov, S, H, out, s, &fle, &fst)) {
             if (fst == ROSAR_OK && fle != cudaSuccess)
                 return set_error(ROSAR_ERR_CUDA, "azimuth_fft: launch failed: %s", cudaGetErrorString(fle));
             return fst;
