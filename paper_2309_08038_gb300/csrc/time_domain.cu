@@ -259,8 +259,8 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             m = ((e >> 4) & 3) * 4 + (e & 1) * 2;
             t = (e >> 6) * 8 + ((e >> 1) & 7);
         };
-        auto prefetch_A = [&](int s2) {
-            const int kk2 = s2 / chunks, m02 = (s2 - kk2 * chunks) * MC;
+        // stage s2 = (tap kk2, samples m02 ..): the caller tracks both (no division per stage)
+        auto prefetch_A = [&](int s2, int kk2, int m02) {
             const int base2 = pmod(th0 + tap_off(kk2), n_az);
             float2 *dst = af + (s2 & 1) * (BT * AFS);
 #pragma unroll
@@ -289,21 +289,25 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             }
             have_y = true;
         };
-        if (stages > 0) prefetch_A(0);
+        if (stages > 0) prefetch_A(0, 0, 0);
         float2 e_run = make_float2(1.f, 0.f);  // fast-time phasor at this thread's first sample of the stage
-        for (int s = 0; s < stages; ++s) {
+        int kk = 0, m0 = 0;                    // tap and first sample of stage s
+        for (int s = 0; s < stages; ++s, m0 += MC) {
+            if (m0 == L) {
+                m0 = 0;
+                ++kk;
+            }
             const int b = s & 1;
             uint8_t *st = stage_base + b * STAGE;
             // a wait that gives up clears ok and every later wait is skipped, but every thread still runs the loop
             // to its end, so the named barriers stay matched (the tile then reads NaN)
             if (s >= 2 && ok) ok = wait_bar(&empty[b], (uint32_t)(((s - 2) >> 1) & 1));
-            const int kk = s / chunks, m0 = (s - kk * chunks) * MC;
-            if (s % chunks == 0) {             // tap boundary: the table of tap kk-1 is no longer read
+            if (m0 == 0) {                     // tap boundary: the table of tap kk-1 is no longer read
                 asm volatile("bar.sync 1, %0;" ::"n"(PRODUCERS) : "memory");
                 if (warp < 2 && kk + 2 < nk) build_tab(kk + 2);
             }
             if (s + 1 < stages) {
-                prefetch_A(s + 1);
+                prefetch_A(s + 1, m0 + MC == L ? kk + 1 : kk, m0 + MC == L ? 0 : m0 + MC);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");       // this thread's copies of stage s
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
