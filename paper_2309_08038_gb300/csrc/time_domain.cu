@@ -253,25 +253,27 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     bool ok = true;
 
     if (producer) {
-        // A copies of one stage: pair e = tid + PRODUCERS*it, row t, samples m, m+1 (see a_pair)
-        auto a_pair = [&](int it, int &t, int &m) {
-            const int e = tid + PRODUCERS * it;
-            m = ((e >> 4) & 3) * 4 + (e & 1) * 2;
-            t = (e >> 6) * 8 + ((e >> 1) & 7);
-        };
+        // A copies of one stage: pair e = tid + PRODUCERS*it (it < 4) is row t = t_a + 32 it, samples m_a, m_a + 1,
+        // with t_a = 8 (tid >> 6) + ((tid >> 1) & 7) and m_a = 4 ((tid >> 4) & 3) + 2 (tid & 1): the same samples and
+        // 8-row group position for every it, so the staging and tile offsets advance by constants
+        constexpr int A_IT = BT * MC / 2 / PRODUCERS;
+        static_assert(A_IT == 4 && PRODUCERS == 256, "the closed form of the A pairs assumes 256 producers");
+        const int m_a = ((tid >> 4) & 3) * 4 + (tid & 1) * 2;
+        const int t_a = (tid >> 6) * 8 + ((tid >> 1) & 7);
+        const int a_src = t_a * AFS + m_a;        // float2 offset in the fp32 staging of a stage, + 32 AFS per it
+        const int a_dst = off(t_a, 2 * m_a);      // byte offset in the operand tiles, + 4 SBO per it
         // stage s2 = (tap kk2, samples m02 ..): the caller tracks both (no division per stage)
         auto prefetch_A = [&](int s2, int kk2, int m02) {
             const int base2 = pmod(th0 + tap_off(kk2), n_az);
-            float2 *dst = af + (s2 & 1) * (BT * AFS);
+            const uint32_t dst = saddr(af + (s2 & 1) * (BT * AFS) + a_src);
+            const float2 *colp = X + m02 + m_a;
 #pragma unroll
-            for (int it = 0; it < BT * MC / 2 / PRODUCERS; ++it) {
-                int t, m;
-                a_pair(it, t, m);
-                int row = base2 + t;
+            for (int it = 0; it < A_IT; ++it) {
+                int row = base2 + t_a + 32 * it;
                 if (wide) row = row >= n_az ? row - n_az : row;
                 else row %= n_az;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst + t * AFS + m)),
-                             "l"(X + (size_t)row * L + m02 + m) : "memory");
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(it * 32 * AFS * 8)),
+                             "l"(colp + (size_t)row * L) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
@@ -289,6 +291,11 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             }
             have_y = true;
         };
+        // B: this thread's (row, 4 samples) slot and its two 16-byte tile offsets, the same every stage
+        const int b_r = 8 * warp + (lane & 7), b_c = lane >> 3;
+        const bool b_swap = (b_r & 4) != 0;
+        const int b_re = off(2 * b_r, 8 * b_c), b_im = off(2 * b_r + 1, 8 * b_c);
+        const int b_first = b_swap ? b_im : b_re, b_second = b_swap ? b_re : b_im;
         if (stages > 0) prefetch_A(0, 0, 0);
         float2 e_run = make_float2(1.f, 0.f);  // fast-time phasor at this thread's first sample of the stage
         int kk = 0, m0 = 0;                    // tap and first sample of stage s
@@ -313,26 +320,24 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             // A: the thread's own 4 pairs of samples, split into the hi and lo tiles
-            const float2 *src = af + b * (BT * AFS);
+            const float2 *src = af + b * (BT * AFS) + a_src;
 #pragma unroll
-            for (int it = 0; it < BT * MC / 2 / PRODUCERS; ++it) {
-                int t, m;
-                a_pair(it, t, m);
-                const float4 a = *reinterpret_cast<const float4 *>(src + t * AFS + m);
+            for (int it = 0; it < A_IT; ++it) {
+                const float4 a = *reinterpret_cast<const float4 *>(src + it * 32 * AFS);
                 uint2 hi, lo;
                 split2(a.x, a.y, hi.x, lo.x);
                 split2(a.z, a.w, hi.y, lo.y);
-                *reinterpret_cast<uint2 *>(st + off(t, 2 * m)) = hi;
-                *reinterpret_cast<uint2 *>(st + TILE + off(t, 2 * m)) = lo;
+                *reinterpret_cast<uint2 *>(st + a_dst + it * 4 * SBO) = hi;
+                *reinterpret_cast<uint2 *>(st + TILE + a_dst + it * 4 * SBO) = lo;
             }
             // B: thread = (row r = 8 warp + (lane & 7), samples 4 (lane >> 3) ..): coefficient x window x phasor by a
             // recurrence over the 4 samples, rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes with r & 4
             // write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
             {
-                const int r = 8 * warp + (lane & 7), c = lane >> 3;
+                const int r = b_r;
                 const float4 t4 = tab[(kk % 3) * BR + r];
                 const float4 st4 = stp[(kk % 3) * BR + r];
-                const int mb = m0 + 4 * c;
+                const int mb = m0 + 4 * b_c;
                 // the thread keeps the same (row, 4 samples) slot every stage: the phasor at its first sample is
                 // taken exactly at the tap's first stage and advanced by MC samples per stage after that
                 e_run = m0 == 0 ? phasor_term(make_float4(1.f, 0.f, t4.z, t4.w), 1.f, (float)mb - p.m_ref)
@@ -348,16 +353,14 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
                     split2(v.y, v.x, im_hi[i], im_lo[i]);
                     e = cmul(e, step);
                 }
-                const bool swap = (r & 4) != 0;
-                const int o_re = off(2 * r, 8 * c), o_im = off(2 * r + 1, 8 * c);
                 const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
                 const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
                 const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
                 const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
-                *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_im : o_re)) = swap ? ih : rh;
-                *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_im : o_re)) = swap ? il : rl;
-                *reinterpret_cast<uint4 *>(st + 2 * TILE + (swap ? o_re : o_im)) = swap ? rh : ih;
-                *reinterpret_cast<uint4 *>(st + 3 * TILE + (swap ? o_re : o_im)) = swap ? rl : il;
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_first) = b_swap ? ih : rh;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_first) = b_swap ? il : rl;
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_second) = b_swap ? rh : ih;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_second) = b_swap ? rl : il;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[b])) : "memory");
