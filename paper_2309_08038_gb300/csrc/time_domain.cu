@@ -262,9 +262,15 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         const int t_a = (tid >> 6) * 8 + ((tid >> 1) & 7);
         const int a_src = t_a * AFS + m_a;        // float2 offset in the fp32 staging of a stage, + 32 AFS per it
         const int a_dst = off(t_a, 2 * m_a);      // byte offset in the operand tiles, + 4 SBO per it
-        // stage s2 = (tap kk2, samples m02 ..): the caller tracks both (no division per stage)
+        // stage s2 = (tap kk2, samples m02 ..): the caller tracks both (no division per stage); the first pulse of
+        // the tap's rows is recomputed only when the tap changes
+        int base_kk = -1, base_row = 0;
         auto prefetch_A = [&](int s2, int kk2, int m02) {
-            const int base2 = pmod(th0 + tap_off(kk2), n_az);
+            if (kk2 != base_kk) {
+                base_kk = kk2;
+                base_row = pmod(th0 + tap_off(kk2), n_az);
+            }
+            const int base2 = base_row;
             const uint32_t dst = saddr(af + (s2 & 1) * (BT * AFS) + a_src);
             const float2 *colp = X + m02 + m_a;
 #pragma unroll
@@ -298,11 +304,12 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         const int b_first = b_swap ? b_im : b_re, b_second = b_swap ? b_re : b_im;
         if (stages > 0) prefetch_A(0, 0, 0);
         float2 e_run = make_float2(1.f, 0.f);  // fast-time phasor at this thread's first sample of the stage
-        int kk = 0, m0 = 0;                    // tap and first sample of stage s
+        int kk = 0, m0 = 0, slot = 0;          // tap, first sample of stage s, and the tap's table slot (kk mod 3)
         for (int s = 0; s < stages; ++s, m0 += MC) {
             if (m0 == L) {
                 m0 = 0;
                 ++kk;
+                slot = slot == 2 ? 0 : slot + 1;
             }
             const int b = s & 1;
             uint8_t *st = stage_base + b * STAGE;
@@ -335,8 +342,8 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             // write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
             {
                 const int r = b_r;
-                const float4 t4 = tab[(kk % 3) * BR + r];
-                const float4 st4 = stp[(kk % 3) * BR + r];
+                const float4 t4 = tab[slot * BR + r];
+                const float4 st4 = stp[slot * BR + r];
                 const int mb = m0 + 4 * b_c;
                 // the thread keeps the same (row, 4 samples) slot every stage: the phasor at its first sample is
                 // taken exactly at the tap's first stage and advanced by MC samples per stage after that
