@@ -269,7 +269,6 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_sc
         phi = torch.from_numpy(rng.standard_normal(cfg.n_az).astype(np.float32) * 0.3).to(device)
         raw_stack[s].copy_(clean * torch.exp(1j * phi)[:, None])
     Bref /= torch.linalg.vector_norm(Bref) / torch.linalg.vector_norm(S_stack)     # comparable scale, detached
-    Bref_r = torch.view_as_real(Bref)
     eps = torch.zeros((n_scans, cfg.n_az), dtype=torch.float32, device=device, requires_grad=True)
     wp = w.clone().requires_grad_(True)
 
@@ -286,8 +285,7 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_sc
             wp.grad = None
             eps.grad = None
             out = forward(method)
-            # ||image - BPA image||^2 as a sum of squares over the real view (one fused torch reduction)
-            loss = torch.nn.functional.mse_loss(torch.view_as_real(out), Bref_r, reduction="sum")
+            loss = rosar.autograd.image_l2_loss(out, Bref)        # ||image - BPA image||^2, one pass each way
             loss.backward()
 
         n = 10
@@ -303,7 +301,7 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, n_sc
             "gather_fwd_px_s": world * pix / t_fg, "gather_fwd_bwd_px_s": world * pix / t_bg,
             "grad_finite": bool(torch.isfinite(wp.grad).all().item() and torch.isfinite(eps.grad).all().item()),
             "note": "step = range compression of the 16 scans (one launch) + phase correction + sparse azimuth filter "
-                    "(forward), torch loss (sum of squares of image - BPA image over the real view), "
+                    "(forward), loss ||image - BPA image||^2 (rosar_image_l2_loss), "
                     "adjoint filter + weight gradient + phase gradient (backward); default = frequency-domain "
                     "kernels (plan from w each step, filter with H / conj(H), cross-spectrum weight gradient), "
                     "gather_* = the gather kernels"}

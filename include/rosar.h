@@ -349,6 +349,24 @@ ROSAR_API rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *g
                                         void *stream);
 
 /*
+ * Image loss of the differentiable form: the squared L2 distance between an image stack and a reference
+ * stack (e.g. back-projection images of the same scans), and its gradient in the same convention:
+ *   loss    = sum_{i<n} |out[i] - ref[i]|^2                       (rosar_image_l2_loss)
+ *   grad[i] = 2 * g * (out[i] - ref[i])                            (rosar_image_l2_loss_grad)
+ * g is the upstream gradient of the loss (a device float).  The sum is deterministic: fixed contiguous chunks
+ * (their number fixed by the library) summed in a fixed order, chunk sums added in double precision in
+ * chunk order.  One read of both stacks per call.
+ *   out, ref  [n] complex (in);  workspace rosar_image_l2_loss_workspace_bytes() bytes of device scratch;
+ *   loss      device float (out);  grad [n] complex (out; may be out or ref itself, no partial overlap).
+ * Errors: null pointers, n < 1, misaligned pointers -> ROSAR_ERR_INVALID_ARG before any launch.
+ */
+ROSAR_API size_t rosar_image_l2_loss_workspace_bytes(void);
+ROSAR_API rosar_status rosar_image_l2_loss(const rosar_c32 *out, const rosar_c32 *ref, long long n, void *workspace,
+                                           float *loss, void *stream);
+ROSAR_API rosar_status rosar_image_l2_loss_grad(const rosar_c32 *out, const rosar_c32 *ref, long long n,
+                                                const float *g, rosar_c32 *grad, void *stream);
+
+/*
  * Adjoint of rosar_range_compress (Eq. (38) transposed):
  *   grad_raw[n][m] = win[m] * sum_l conj(c_l) * exp(+j*2*pi*l*m/L) * g[l][n]
  *   g [L][n_az] range-major (in); grad_raw [n_az][L] pulse-major (out).

@@ -9,7 +9,7 @@ from ._lib import LIB_PATH, RosarError, load  # noqa: F401
 from .ops import (Radar, azimuth_fft_supported, azimuth_plan, bpa, image, image_fft, image_noalloc,  # noqa: F401
                   range_compress, sparse_azimuth, sparse_azimuth_fft)
 from .ops import azimuth_weight_grad_fft, bpa_time, image_fft_host, sas_time, sparse_azimuth_fft_scans  # noqa: F401
-from .ops import image_fft_scans, image_fft_scans_pipelined  # noqa: F401
+from .ops import image_fft_scans, image_fft_scans_pipelined, image_l2_loss, image_l2_loss_grad  # noqa: F401
 from .ops import (image_migrating, phase_apply, phase_grad, range_compress_adjoint,  # noqa: F401
                   sparse_azimuth_adjoint, sparse_azimuth_migrating, sparse_azimuth_scans)
 from .batch import Batch, Tuning  # noqa: F401

@@ -70,6 +70,9 @@ _PROTOS = {
     "rosar_sparse_azimuth_scans": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_phase_grad": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "rosar_image_l2_loss_workspace_bytes": (ctypes.c_size_t, []),
+    "rosar_image_l2_loss": (_I, [_P, _P, ctypes.c_longlong, _P, _P, _P]),
+    "rosar_image_l2_loss_grad": (_I, [_P, _P, ctypes.c_longlong, _P, _P, _P]),
     "rosar_range_compress_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "rosar_range_compress_adjoint_scans": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_batch_workspace_bytes": (ctypes.c_size_t, [_I]),

@@ -3,6 +3,7 @@
 SparseAzimuthPhase:  out = sparse_azimuth(S * exp(j*eps), w, o) for a stack of scans sharing w;
                      gradients in S, eps (per scan and pulse) and w; gather or frequency-domain kernels.
 RangeCompress:       S = range_compress(raw, win); gradient in raw through the adjoint FFT tile.
+ImageL2Loss:         sum |out - ref|^2 and its gradient, one library pass each way.
 
 Both follow torch's convention for complex tensors (the gradient passed around is the
 conjugate-Wirtinger derivative of the real loss), so they compose with torch ops on either side.
@@ -61,6 +62,28 @@ class RangeCompress(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         return ops.range_compress_adjoint(g.contiguous(), ctx.win, centred=ctx.centred), None, None
+
+
+class ImageL2Loss(torch.autograd.Function):
+    """loss = sum |out - ref|^2 in one library pass each way (rosar_image_l2_loss / _grad); ref may also
+    require a gradient (its gradient is the negative of out's)."""
+
+    @staticmethod
+    def forward(ctx, out, ref):
+        out, ref = out.contiguous(), ref.contiguous()
+        ctx.save_for_backward(out, ref)
+        return ops.image_l2_loss(out, ref)
+
+    @staticmethod
+    def backward(ctx, g):
+        out, ref = ctx.saved_tensors
+        grad = ops.image_l2_loss_grad(out, ref, g.to(torch.float32).contiguous())
+        return grad, (-grad if ctx.needs_input_grad[1] else None)
+
+
+def image_l2_loss(out, ref):
+    """Differentiable squared L2 distance between two complex stacks (e.g. images and reference images)."""
+    return ImageL2Loss.apply(out, ref)
 
 
 # the frequency-domain forms keep three rows of n_az in shared memory for the weight gradient

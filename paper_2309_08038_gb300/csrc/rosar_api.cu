@@ -506,6 +506,35 @@ rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *grad_S_t, c
                              static_cast<cudaStream_t>(stream));
 }
 
+size_t rosar_image_l2_loss_workspace_bytes(void) { return sizeof(double) * (size_t)image_loss_partials(); }
+
+rosar_status rosar_image_l2_loss(const rosar_c32 *out, const rosar_c32 *ref, long long n, void *workspace,
+                                 float *loss, void *stream) {
+    clear_error();
+    if (!out || !ref || !workspace || !loss) return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss: null pointer argument");
+    if (n < 1) return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss: n=%lld < 1", n);
+    if (misaligned(out, 8) || misaligned(ref, 8) || misaligned(workspace, 8) || misaligned(loss, 4))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss: misaligned pointer");
+    return launch_image_l2_loss(reinterpret_cast<const float2 *>(out), reinterpret_cast<const float2 *>(ref), n,
+                                static_cast<double *>(workspace), loss, static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_image_l2_loss_grad(const rosar_c32 *out, const rosar_c32 *ref, long long n, const float *g,
+                                      rosar_c32 *grad, void *stream) {
+    clear_error();
+    if (!out || !ref || !g || !grad) return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss_grad: null pointer argument");
+    if (n < 1) return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss_grad: n=%lld < 1", n);
+    if (misaligned(out, 8) || misaligned(ref, 8) || misaligned(grad, 8) || misaligned(g, 4))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss_grad: misaligned pointer");
+    const size_t bytes = sizeof(rosar_c32) * (size_t)n;
+    if (overlaps(grad, bytes, out, bytes) && grad != out)
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss_grad: grad partially overlaps out");
+    if (overlaps(grad, bytes, ref, bytes) && grad != ref)
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_l2_loss_grad: grad partially overlaps ref");
+    return launch_image_l2_loss_grad(reinterpret_cast<const float2 *>(out), reinterpret_cast<const float2 *>(ref), n,
+                                     g, reinterpret_cast<float2 *>(grad), static_cast<cudaStream_t>(stream));
+}
+
 rosar_status rosar_range_compress_adjoint(const rosar_c32 *g, const float *win, int n_az, int L, int centred,
                                           rosar_c32 *grad_raw, void *stream) {
     clear_error();

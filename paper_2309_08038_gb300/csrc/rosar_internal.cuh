@@ -86,6 +86,13 @@ rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, in
 // Azimuth filter in the frequency domain (azimuth_fft.cu).
 int azimuth_fft_supported(int n_az);
 
+// Image loss of the differentiable form (image_loss.cu): partial sums per call = image_loss_partials().
+int image_loss_partials();
+rosar_status launch_image_l2_loss(const float2 *out, const float2 *ref, long long n, double *partial, float *loss,
+                                  cudaStream_t s);
+rosar_status launch_image_l2_loss_grad(const float2 *out, const float2 *ref, long long n, const float *g,
+                                       float2 *grad, cudaStream_t s);
+
 // Pipelined multi-scan imaging (image_pipeline.cu): 1 if a stage kernel exists for (L, n_az).
 int image_pipeline_supported(int L, int n_az);
 rosar_status launch_image_pipeline(const float2 *raw, const float *win, const float2 *H, int n_scans, int n_az, int L,

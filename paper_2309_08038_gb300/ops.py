@@ -399,6 +399,31 @@ def range_compress_adjoint(g, win=None, centred=True, out=None, stream=None):
     return out
 
 
+def image_l2_loss(out, ref, stream=None):
+    """rosar_image_l2_loss: sum |out - ref|^2 over two complex stacks of one shape, as a 0-d float32 tensor
+    (deterministic order)."""
+    lib = _lib.load()
+    require(out, torch.complex64, "out")
+    require(ref, torch.complex64, "ref", shape=tuple(out.shape))
+    ws = torch.empty(int(lib.rosar_image_l2_loss_workspace_bytes()) // 8, dtype=torch.float64, device=out.device)
+    loss = torch.empty((), dtype=torch.float32, device=out.device)
+    check(lib.rosar_image_l2_loss(ptr(out), ptr(ref), out.numel(), ptr(ws), ptr(loss), stream_handle(stream)))
+    return loss
+
+
+def image_l2_loss_grad(out, ref, g, grad=None, stream=None):
+    """rosar_image_l2_loss_grad: 2 g (out - ref) for the upstream gradient g (a 0-d float32 CUDA tensor)."""
+    lib = _lib.load()
+    require(out, torch.complex64, "out")
+    require(ref, torch.complex64, "ref", shape=tuple(out.shape))
+    require(g, torch.float32, "g", shape=())
+    if grad is None:
+        grad = torch.empty_like(out)
+    require(grad, torch.complex64, "grad", shape=tuple(out.shape))
+    check(lib.rosar_image_l2_loss_grad(ptr(out), ptr(ref), out.numel(), ptr(g), ptr(grad), stream_handle(stream)))
+    return grad
+
+
 # ------------------------------------------------------------ range-migration-aware taps --
 
 def sparse_azimuth_migrating(S, w, o, dl, n_rng=None, out=None, stream=None):

@@ -143,6 +143,19 @@ def test_stacked_range_calls_reject_bad_arguments(lib):
         assert f(raw, None, 2, 360, 64, 1, ctypes.c_void_p(0x10000000 + 360 * 64 * 8), None) == 1   # overlap
 
 
+def test_image_loss_rejects_bad_arguments(lib):
+    a, b, ws, out = (ctypes.c_void_p(x) for x in (0x10000000, 0x20000000, 0x30000000, 0x40000000))
+    assert lib.rosar_image_l2_loss_workspace_bytes() >= 8
+    f, fg = lib.rosar_image_l2_loss, lib.rosar_image_l2_loss_grad
+    assert f(None, b, 10, ws, out, None) == 1                                  # no image
+    assert f(a, b, 0, ws, out, None) == 1                                      # empty
+    assert f(a, b, 10, None, out, None) == 1                                   # no workspace
+    assert f(ctypes.c_void_p(0x10000004), b, 10, ws, out, None) == 1           # misaligned
+    assert fg(a, b, 10, None, out, None) == 1                                  # no upstream gradient
+    assert fg(a, b, -1, out, out, None) == 1                                   # empty
+    assert fg(a, b, 10, out, ctypes.c_void_p(0x10000008), None) == 1           # grad partly overlaps out
+
+
 def test_image_rejects_bad_arguments(lib):
     f = lib.rosar_image
     assert f(FAKE, None, FAKE, FAKE, 0, 100, 60, 8, FAKE2, ctypes.c_void_p(0x40000000), None) == 2

@@ -115,6 +115,28 @@ def test_range_compress_autograd_stack(rosar):
         assert _rel(t.grad[s].cpu().numpy(), ref) < 1e-5, s
 
 
+@pytest.mark.parametrize("shape", [(1,), (7,), (3, 257), (16, 256, 3600)])
+def test_image_l2_loss_and_gradient(rosar, shape):
+    """rosar_image_l2_loss against the FP64 sum of |out - ref|^2 (ragged sizes down to one element and the
+    differentiable workload's 16-scan stack), bit-identical on repeated calls; the autograd gradient against
+    2 g (out - ref), and ref's gradient its negative."""
+    import torch
+    rng = np.random.default_rng(len(shape) + shape[-1])
+    out, ref = _c(rng, *shape), _c(rng, *shape)
+    to, tr = _cuda(torch, out), _cuda(torch, ref)
+    loss = rosar.image_l2_loss(to, tr)
+    exact = float(np.sum(np.abs(out.astype(np.complex128) - ref.astype(np.complex128)) ** 2))
+    assert abs(loss.item() - exact) <= 1e-6 * exact
+    assert torch.equal(loss, rosar.image_l2_loss(to, tr))
+    a = to.clone().requires_grad_(True)
+    b = tr.clone().requires_grad_(True)
+    l2 = rosar.autograd.image_l2_loss(a, b)
+    (3.0 * l2).backward()
+    d = (out.astype(np.complex128) - ref.astype(np.complex128)) * 6.0
+    assert _rel(a.grad.cpu().numpy(), d) < 1e-6
+    assert torch.equal(b.grad, -a.grad)
+
+
 def _crop_problem(seed=3):
     """The 64-pulse crop: 64 pulses, 32 range rows, K = 16 taps of M = 32, two scans."""
     rng = np.random.default_rng(seed)
