@@ -290,12 +290,15 @@ def test_highres_full_size_sampled_rows(rosar, torch):
             assert not np.any(got_rows[i]), r
             continue
         assert rel_l2(got_rows[i], ref[i]) < TOL_IMAGE, r
-    # BPA on the same range-compressed data, sampled pixels
+    # FFT+BPA (Sec. III-D, w_BP) on sampled pixels: the GPU chain (range compression, then BPA) against
+    # the oracle chain on the same raw cube; the oracle's range bins come from its own DFT, and only the
+    # bins the sampled rows' interpolation can touch are evaluated
     S = rosar.range_compress(dev(torch, raw), dev(torch, win))
     b = host(rosar.bpa(S, api_radar(rosar, cfg), cfg.L, cfg.M_ap)[[5, 700]])
-    Sh = np.zeros((cfg.L, cfg.n_az), dtype=np.complex64)
     need = sorted({l for r in (5, 700) for l in range(r - 2, r + 12) if 0 <= l < cfg.L})
-    Sh[need] = S[need].cpu().numpy()
+    Sh = np.zeros((cfg.L, cfg.n_az), dtype=np.complex128)
+    Sh[need] = O.range_compress(raw, win, bins=need)
+    assert rel_l2(host(S[need]), Sh[need]) < TOL_FFT
     th = np.arange(0, cfg.n_az, 97)
     for i, r in enumerate((5, 700)):
         ref_b = O.bpa_pixels(Sh, oracle_radar(cfg), cfg.n_az, cfg.M_ap, np.full(th.size, r), th)
