@@ -419,7 +419,15 @@ typedef struct rosar_batch_tuning {
     int spin_limit;         /* polls (~0.1 us apart) before a dependency wait gives up; 0 selects 2^24 */
     int debug_unmet_scan;   /* test hook, -1 = off: scan whose azimuth tiles wait for one range tile
                                more than exists, so that their wait must time out */
+    int mix;                /* interleave >= 2: the range tiles of scan s+d-1 and the azimuth tiles of scan s
+                               alternate in `mix` chunks each (1..32; 0 selects 1: one block each) */
+    int flags;              /* ROSAR_BATCH_* bits, 0 = none */
 } rosar_batch_tuning;
+
+/* Whole-row FFT tiles drop each S row from L2 once they have read it, so range-compressed data that is
+ * still cached is never written back to memory: the scans' S buffers (scratch) hold undefined values after
+ * the launch. */
+#define ROSAR_BATCH_DISCARD_S 2
 
 typedef struct rosar_batch rosar_batch;   /* opaque host handle */
 

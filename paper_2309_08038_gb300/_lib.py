@@ -38,7 +38,8 @@ class ScanStruct(ctypes.Structure):
 
 class BatchTuningStruct(ctypes.Structure):
     _fields_ = [("az_tile", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("interleave", ctypes.c_int),
-                ("spin_limit", ctypes.c_int), ("debug_unmet_scan", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int), ("debug_unmet_scan", ctypes.c_int), ("mix", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -100,9 +100,18 @@ def choose_azimuth(n_rng: int, n_az: int, K: int, per_row: bool = False, reps: i
     return res
 
 
-def batch_candidates():
-    """The tuning space: azimuth tile width x persistent CTAs per SM x tile order."""
+def batch_candidates(fft_tiles: bool = True):
+    """The tuning space.  Whole-row FFT tiles: tile order (all range tiles first; range tiles 1 or 2 scans ahead of
+    the azimuth tiles, in one block or alternating in 8 chunks per scan) x dropping S from L2 once read.  Gather
+    tiles: azimuth tile width x persistent CTAs per SM x tile order."""
+    from .batch import DISCARD_S
     out = []
+    if fft_tiles:
+        for flags in (0, DISCARD_S):
+            out.append(Tuning(interleave=0, flags=flags))
+            for interleave, mix in ((2, 1), (3, 1), (3, 8)):
+                out.append(Tuning(interleave=interleave, mix=mix, flags=flags))
+        return out
     for az_tile in (512, 1024, 2048):
         for ctas in (0, 2):
             for interleave in (0, 1, 2, 3):
@@ -113,7 +122,7 @@ def batch_candidates():
 def _batch_key(scans) -> str:
     shapes = sorted((tuple(s["raw"].shape), s["w"].shape[1], s["o"].dim(), s.get("H") is not None) for s in scans)
     h = hashlib.sha1(repr(shapes).encode()).hexdigest()[:16]
-    return f"batch/{_gpu()}/{len(scans)}scans/{h}"
+    return f"batch2/{_gpu()}/{len(scans)}scans/{h}"
 
 
 def tune_batch(scans, candidates=None, reps: int = 3, use_cache: bool = True) -> dict:
@@ -123,7 +132,7 @@ def tune_batch(scans, candidates=None, reps: int = 3, use_cache: bool = True) ->
         hit = _load().get(key)
         if hit is not None:
             return {"tuning": Tuning(**hit["tuning"]), "ms": hit["ms"], "cached": True}
-    cands = candidates or batch_candidates()
+    cands = candidates or batch_candidates(all(s.get("H") is not None for s in scans))
     ms = {}
     best, best_ms = None, float("inf")
     for t in cands:
@@ -131,7 +140,7 @@ def tune_batch(scans, candidates=None, reps: int = 3, use_cache: bool = True) ->
         m = _time_ms(b.launch, reps, warmup=1)
         b.status()
         b.close()
-        name = f"az{t.az_tile}_cta{t.ctas_per_sm}_il{t.interleave}"
+        name = f"az{t.az_tile}_cta{t.ctas_per_sm}_il{t.interleave}_mix{t.mix}_f{t.flags}"
         ms[name] = m
         if m < best_ms:
             best, best_ms = t, m

@@ -15,17 +15,23 @@ from ._lib import check, require, stream_handle
 class Tuning:
     """Mirrors rosar_batch_tuning.  az_tile in {256, 512, 1024, 2048}; ctas_per_sm 0 = occupancy limit;
     interleave 0 = all range tiles first, 1 = scan by scan, d >= 2 = range tiles d-1 scans ahead of the azimuth
-    tiles; spin_limit 0 = default."""
+    tiles; spin_limit 0 = default; mix = chunks per scan in which the two kinds of tile alternate (interleave
+    >= 2); flags = DISCARD_S bit."""
 
     az_tile: int = 1024
     ctas_per_sm: int = 0
     interleave: int = 0
     spin_limit: int = 0
     debug_unmet_scan: int = -1
+    mix: int = 1
+    flags: int = 0
 
     def as_struct(self):
         return _lib.BatchTuningStruct(self.az_tile, self.ctas_per_sm, self.interleave, self.spin_limit,
-                                      self.debug_unmet_scan)
+                                      self.debug_unmet_scan, self.mix, self.flags)
+
+
+DISCARD_S = 2     # ROSAR_BATCH_DISCARD_S
 
 
 class Batch:

@@ -4,11 +4,18 @@
 // (fft_tile.cuh) on P = 4096/L pulses of one scan with the CTA's 256 threads; an
 // azimuth tile runs the gather-MAC tile (azimuth_tile.cuh) on 256*J outputs of one
 // row of one scan, or, for a scan given its frequency-domain plan H, the whole row
-// through the row FFT (row_fft.cuh): forward transform, product with H, inverse.  Tickets are handed out by an atomic counter, range tiles of a
-// scan always before its azimuth tiles; the scan's done-counter is bumped (release)
-// after each range tile, and an azimuth tile's thread 0 polls it (acquire) before
-// the CTA reads S through L2.  The poll is bounded; on expiry the kernel raises an
-// error word that every CTA checks before taking its next ticket.
+// through the row FFT (row_fft.cuh): forward transform, product with H, inverse.
+// Tickets are handed out by an atomic counter, range tiles of a scan always before
+// its azimuth tiles; the scan's done-counter is bumped (release) after each range
+// tile, and an azimuth tile's thread 0 polls it (acquire) before the CTA reads S
+// through L2.  The poll is bounded; on expiry the kernel raises an error word that
+// every CTA checks before taking its next ticket.
+//
+// Keeping S in L2: with interleave d >= 2 the range tiles of scan s+d-1 and the
+// azimuth tiles of scan s alternate in `mix` chunks each, so a scan's S is read
+// back while it is still in L2, and with DISCARD_S whole-row FFT tiles drop each
+// S row from L2 once read, so S, a scratch buffer, is not written back to memory
+// while it stays cached.  A CTA takes its next ticket when it starts a tile.
 
 #include <stdlib.h>
 #include <string.h>
@@ -43,7 +50,11 @@ struct Segment {
     int scan;
     int kind;    // 0 range tiles, 1 azimuth tiles
     int count;
+    int start;   // tile index (within the scan's tiles of this kind) of the segment's first ticket
 };
+
+constexpr int MIX_MAX = 32;              // chunks per scan and kind
+constexpr int SEGS_PER_SCAN = 2 * MIX_MAX;
 
 // counters[0] ticket head, [1] error flag, [2] scan that timed out, [3] unused, [4 + s] range tiles done of scan s
 constexpr int CNT_HEAD = 0, CNT_ERR = 1, CNT_ERR_SCAN = 2, CNT_DONE = 4;
@@ -71,7 +82,7 @@ __device__ __forceinline__ void run_range(const ScanDev &sc, int n0, char *sm, b
 // lengths with a compile-time plan run the fused filter (first and last passes on global memory, H read from
 // global in the fused middle step); the others load the row, eight loads in flight per thread, and run the
 // run-time plan.
-__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem) {
+__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem, bool discard) {
     const int N = sc.n_az;
     float2 *x = reinterpret_cast<float2 *>(smem);
     float2 *tw = x + rowfft::padded_len(N);
@@ -82,9 +93,9 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
     if (sc.fixed) {
         __syncthreads();
         switch (sc.fixed) {                   // the run-time plan's radices, constant strides
-            case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
-            case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
-            default: rowfft::row_filter_fused<7200, BT_THREADS, false, 8, 4, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf); break;
+            case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
+            case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
+            default: rowfft::row_filter_fused<7200, BT_THREADS, false, 8, 4, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
         }
         __syncthreads();
         return;
@@ -117,34 +128,44 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
     __syncthreads();
 }
 
+__device__ __forceinline__ int find_segment(const Segment *__restrict__ segs, int n_segs, int t) {
+    int lo = 0, hi = n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&segs[mid].first) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int J>
 __global__ void __launch_bounds__(BT_THREADS, 3)
 batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs, int n_segs, int total,
-             int *counters, int spin_limit, int debug_scan) {
+             int *counters, int spin_limit, int debug_scan, int flags) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int red[4 * az::THREADS / 32];
-    __shared__ int s_ticket, s_abort;
+    __shared__ int s_ticket[2], s_abort;
     int *head = counters + CNT_HEAD, *err = counters + CNT_ERR, *done = counters + CNT_DONE;
+    const bool discard = (flags & ROSAR_BATCH_DISCARD_S) != 0;
     int tab_L = 0;   // L of the twiddle table left in shared memory by the previous range tile
 
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int t = atomicAdd(head, 1);
-            if (t < total && ld_relaxed(err) != 0) t = total;
-            s_ticket = t;
-            s_abort = 0;
-        }
-        __syncthreads();
-        const int t = s_ticket;
+    // a CTA holds two tickets: the tile it runs and the next one, taken when the current tile starts (the
+    // smallest unfinished ticket is always some CTA's current tile, and its dependencies have smaller tickets,
+    // so every wait ends)
+    constexpr int GRAB = 32;   // the thread that takes tickets (warp 1: thread 0 does the dependency waits)
+    if (threadIdx.x == GRAB) s_ticket[0] = atomicAdd(head, 1);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const int t = s_ticket[cur];
         if (t >= total) break;
-        int lo = 0, hi = n_segs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&segs[mid].first) <= t) lo = mid; else hi = mid - 1;
-        }
-        const Segment sg = segs[lo];
+        const Segment sg = segs[find_segment(segs, n_segs, t)];
         const ScanDev sc = scans[sg.scan];
-        const int local = t - sg.first;
+        const int local = t - sg.first + sg.start;
+        if (threadIdx.x == 0) s_abort = 0;
+        if (threadIdx.x == GRAB) {
+            int nt = atomicAdd(head, 1);
+            if (nt < total && ld_relaxed(err) != 0) nt = total;
+            s_ticket[cur ^ 1] = nt;
+        }
         if (sg.kind == 0) {
             const bool build = tab_L != sc.L;
             const int n0 = local * sc.P;
@@ -179,17 +200,18 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
             __syncthreads();
             if (s_abort) break;
             if (sc.H) {
-                fft_row_tile(sc, local, sm);
+                fft_row_tile(sc, local, sm, discard);
             } else {
                 const int r = local / sc.az_tiles_per_row;
                 const int th0 = (local - r * sc.az_tiles_per_row) * az::Geo<J>::TW;
                 az::azimuth_tile<J, true>(sc.S, sc.w, sc.o, sc.o_row_stride, sc.n_az, sc.K, sc.out, r, th0, sm, red);
             }
         }
+        __syncthreads();           // the tile is done with shared memory; the next ticket is visible
     }
 }
 
-using KernelFn = void (*)(const ScanDev *, const Segment *, int, int, int *, int, int);
+using KernelFn = void (*)(const ScanDev *, const Segment *, int, int, int *, int, int, int);
 
 KernelFn kernel_for(int J) {
     switch (J) {
@@ -247,7 +269,7 @@ extern "C" {
 
 size_t rosar_batch_workspace_bytes(int n_scans) {
     if (n_scans < 1) return 0;
-    return align256(sizeof(ScanDev) * (size_t)n_scans) + align256(sizeof(Segment) * 2 * (size_t)n_scans) +
+    return align256(sizeof(ScanDev) * (size_t)n_scans) + align256(sizeof(Segment) * SEGS_PER_SCAN * (size_t)n_scans) +
            align256(sizeof(int) * (CNT_DONE + (size_t)n_scans));
 }
 
@@ -262,18 +284,23 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
                          rosar_batch_workspace_bytes(n_scans));
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
         return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: workspace must be 256-byte aligned");
-    rosar_batch_tuning tn = {1024, 0, 0, 1 << 24, -1};
+    rosar_batch_tuning tn = {1024, 0, 0, 1 << 24, -1, 1, 0};
     if (tuning) tn = *tuning;
     if (tn.az_tile == 0) tn.az_tile = 1024;
     if (tn.spin_limit <= 0) tn.spin_limit = 1 << 24;
+    if (tn.mix <= 0) tn.mix = 1;
     if (tn.interleave < 0 || tn.interleave > 8)
         return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: interleave=%d not in [0, 8]", tn.interleave);
+    if (tn.mix > MIX_MAX)
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: mix=%d not in [1, %d]", tn.mix, MIX_MAX);
+    if (tn.flags & ~ROSAR_BATCH_DISCARD_S)
+        return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: unknown flags 0x%x", tn.flags);
     const int J = tn.az_tile / az::THREADS;
     if (tn.az_tile % az::THREADS || (J != 1 && J != 2 && J != 4 && J != 8))
         return set_error(ROSAR_ERR_INVALID_ARG, "batch_create: az_tile=%d not in {256, 512, 1024, 2048}", tn.az_tile);
 
     ScanDev *hs = static_cast<ScanDev *>(calloc((size_t)n_scans, sizeof(ScanDev)));
-    Segment *hg = static_cast<Segment *>(calloc(2 * (size_t)n_scans, sizeof(Segment)));
+    Segment *hg = static_cast<Segment *>(calloc(SEGS_PER_SCAN * (size_t)n_scans, sizeof(Segment)));
     if (!hs || !hg) {
         free(hs);
         free(hg);
@@ -341,27 +368,35 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
     // ticket order.  Azimuth tiles of a scan always come after all of its range tiles, so every range tile an
     // azimuth tile waits for has been handed to a running CTA (which waits on nothing) before it.
     int first = 0, ns = 0;
-    auto range_seg = [&](int s) {
-        hg[ns++] = {first, s, 0, hs[s].range_tiles};
-        first += hs[s].range_tiles;
+    auto push = [&](int s, int kind, int start, int count) {
+        if (count > 0) {
+            hg[ns++] = {first, s, kind, count, start};
+            first += count;
+        }
     };
-    auto az_seg = [&](int s) {
-        const int na = hs[s].az_tiles_per_row * hs[s].L;
-        hg[ns++] = {first, s, 1, na};
-        first += na;
-    };
+    auto n_range = [&](int s) { return hs[s].range_tiles; };
+    auto n_az = [&](int s) { return hs[s].az_tiles_per_row * hs[s].L; };
     if (tn.interleave >= 1) {
         // range tiles run (interleave - 1) scans ahead of the azimuth tiles: 1 = scan by scan, 2 = the next
-        // scan's range tiles before this scan's azimuth tiles (its S is produced while this one is filtered)
+        // scan's range tiles alongside this scan's azimuth tiles (its S is produced while this one is
+        // filtered).  With mix = m the two lists alternate in m chunks each (range chunk first).
         const int ahead = tn.interleave - 1;
-        for (int s = 0; s < n_scans && s < ahead; ++s) range_seg(s);
+        for (int s = 0; s < n_scans && s < ahead; ++s) push(s, 0, 0, n_range(s));
         for (int s = 0; s < n_scans; ++s) {
-            if (s + ahead < n_scans) range_seg(s + ahead);
-            az_seg(s);
+            const int rs = s + ahead;
+            const int nr = (rs < n_scans && ahead > 0) ? n_range(rs) : 0, na = n_az(s);
+            if (ahead == 0) push(s, 0, 0, n_range(s));
+            const int m = ahead > 0 ? tn.mix : 1;
+            for (int c = 0; c < m; ++c) {
+                const int r0 = (int)((long long)nr * c / m), r1 = (int)((long long)nr * (c + 1) / m);
+                const int a0 = (int)((long long)na * c / m), a1 = (int)((long long)na * (c + 1) / m);
+                push(rs, 0, r0, r1 - r0);
+                push(s, 1, a0, a1 - a0);
+            }
         }
     } else {
-        for (int s = 0; s < n_scans; ++s) range_seg(s);
-        for (int s = 0; s < n_scans; ++s) az_seg(s);
+        for (int s = 0; s < n_scans; ++s) push(s, 0, 0, n_range(s));
+        for (int s = 0; s < n_scans; ++s) push(s, 1, 0, n_az(s));
     }
     const int total = first;
 
@@ -369,7 +404,7 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
     ScanDev *d_scans = reinterpret_cast<ScanDev *>(ws);
     Segment *d_segs = reinterpret_cast<Segment *>(ws + align256(sizeof(ScanDev) * (size_t)n_scans));
     int *d_cnt = reinterpret_cast<int *>(ws + align256(sizeof(ScanDev) * (size_t)n_scans) +
-                                         align256(sizeof(Segment) * 2 * (size_t)n_scans));
+                                         align256(sizeof(Segment) * SEGS_PER_SCAN * (size_t)n_scans));
     cudaError_t e = cudaMemcpy(d_scans, hs, sizeof(ScanDev) * (size_t)n_scans, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_segs, hg, sizeof(Segment) * (size_t)ns, cudaMemcpyHostToDevice);
     free(hs);
@@ -402,7 +437,8 @@ rosar_status rosar_batch_create(const rosar_scan *scans, int n_scans, const rosa
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(d_cnt, 0, sizeof(int) * (CNT_DONE + (size_t)n_scans), cs);
-        fn<<<grid, BT_THREADS, smem, cs>>>(d_scans, d_segs, ns, total, d_cnt, tn.spin_limit, tn.debug_unmet_scan);
+        fn<<<grid, BT_THREADS, smem, cs>>>(d_scans, d_segs, ns, total, d_cnt, tn.spin_limit, tn.debug_unmet_scan,
+                                           tn.flags);
         e = cudaStreamEndCapture(cs, &b->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);

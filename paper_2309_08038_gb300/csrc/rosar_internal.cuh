@@ -26,8 +26,14 @@ rosar_status ensure_smem(const void *func, size_t bytes, int *limits, const char
 
 // ------------------------------------------------------------ complex ops --
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract, and a real multiple of a complex added to another, each as ONE packed FP32x2
+// instruction (sm_100 and later): per lane the same IEEE round-to-nearest result as the scalar expression,
+// in half the issue slots of two scalar instructions.  The transforms are issue-bound, and most of a
+// butterfly's arithmetic is these three forms.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a + s*b for real s (one rounding per lane, as fmaf(s, b.x, a.x), fmaf(s, b.y, a.y))
+__device__ __forceinline__ float2 caxpy(float s, float2 b, float2 a) { return __ffma2_rn(make_float2(s, s), b, a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -38,7 +44,7 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
     acc.y = fmaf(a.x, b.y, acc.y);
     acc.y = fmaf(a.y, b.x, acc.y);
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization may start

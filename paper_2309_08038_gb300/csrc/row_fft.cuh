@@ -48,11 +48,10 @@ __device__ __forceinline__ void small_dft<3>(float2 *v) {
     constexpr float h = 0.86602540378443865f;   // sin(2*pi/3)
     const float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
     const float2 y0 = cadd(v[0], t1);
-    const float2 a = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
-    const float2 b = make_float2(h * t2.x, h * t2.y);           // y1 = a - i b, y2 = a + i b
+    const float2 a = caxpy(-0.5f, t1, v[0]);                     // y1 = a - i h t2, y2 = a + i h t2
     v[0] = y0;
-    v[1] = make_float2(a.x + b.y, a.y - b.x);
-    v[2] = make_float2(a.x - b.y, a.y + b.x);
+    v[1] = make_float2(fmaf(h, t2.y, a.x), fmaf(-h, t2.x, a.y));
+    v[2] = make_float2(fmaf(-h, t2.y, a.x), fmaf(h, t2.x, a.y));
 }
 
 template <>
@@ -72,11 +71,11 @@ __device__ __forceinline__ void small_dft<5>(float2 *v) {
     const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
     const float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
     const float2 x0 = v[0];
-    const float2 a1 = make_float2(fmaf(c1, t1.x, fmaf(c2, t2.x, x0.x)), fmaf(c1, t1.y, fmaf(c2, t2.y, x0.y)));
-    const float2 a2 = make_float2(fmaf(c2, t1.x, fmaf(c1, t2.x, x0.x)), fmaf(c2, t1.y, fmaf(c1, t2.y, x0.y)));
-    const float2 b1 = make_float2(fmaf(s1, t3.x, s2 * t4.x), fmaf(s1, t3.y, s2 * t4.y));
-    const float2 b2 = make_float2(fmaf(s2, t3.x, -s1 * t4.x), fmaf(s2, t3.y, -s1 * t4.y));
-    v[0] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+    const float2 a1 = caxpy(c1, t1, caxpy(c2, t2, x0));
+    const float2 a2 = caxpy(c2, t1, caxpy(c1, t2, x0));
+    const float2 b1 = caxpy(s1, t3, cscale(t4, s2));
+    const float2 b2 = caxpy(s2, t3, cscale(t4, -s1));
+    v[0] = cadd(cadd(x0, t1), t2);
     v[1] = make_float2(a1.x + b1.y, a1.y - b1.x);              // a1 - i b1
     v[4] = make_float2(a1.x - b1.y, a1.y + b1.x);              // a1 + i b1
     v[2] = make_float2(a2.x + b2.y, a2.y - b2.x);              // a2 - i b2
@@ -298,10 +297,12 @@ __device__ __forceinline__ void dit_seq(float2 *x, const float2 *tc, const float
 
 // First DIF pass (M = N, stride s = N/R) with its inputs read from global memory (ld.cg: src may have been
 // written earlier by the same kernel).  WAIT_ASYNC: the thread's cp.async copies (the H row) complete before
-// the closing barrier, so they are visible to the whole CTA after it.
+// the closing barrier, so they are visible to the whole CTA after it.  discard: src is scratch that nothing
+// reads again, so after the barrier (every element has been read) the 128-byte L2 lines lying wholly inside
+// the row are dropped without being written back to memory; the lines it shares with neighbouring rows stay.
 template <int N, int R, int T, bool WAIT_ASYNC>
 __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src, float2 *x, const float2 *tc,
-                                                 const float2 *tf) {
+                                                 const float2 *tf, bool discard = false) {
     constexpr int s = N / R;
 #pragma unroll 1
     for (int j = threadIdx.x; j < s; j += T) {
@@ -317,6 +318,12 @@ __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src,
     }
     if (WAIT_ASYNC) cp_async_wait<0>();
     __syncthreads();
+    if (discard) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+        const uintptr_t first = (a + 127) & ~(uintptr_t)127, end = (a + sizeof(float2) * (size_t)N) & ~(uintptr_t)127;
+        for (uintptr_t l = first + 128 * (uintptr_t)threadIdx.x; l < end; l += 128 * (uintptr_t)T)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(l) : "memory");
+    }
 }
 
 // Last forward pass (blocks of R, stride 1), y = conj(H . X) (conj(H) . X conjugated when hs = -1), and the
@@ -378,12 +385,14 @@ __device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float 
 
 // src, dst: the row in global memory (natural order); x: N elements of shared memory (no padding); the
 // caller has built the twiddle table and synchronised.  With H_SMEM, h may still be arriving by cp.async
-// when this starts (waited for at the end of the first pass).  No barrier at the end.
+// when this starts (waited for at the end of the first pass).  No barrier at the end.  discard: src is
+// scratch, dropped from L2 once read (dif_first_global).
 template <int N, int T, bool H_SMEM, int R1, int... Rs>
 __device__ __forceinline__ void row_filter_fused(const float2 *__restrict__ src, const float2 *h, float hs, float2 *x,
-                                                 float2 *__restrict__ dst, const float2 *tc, const float2 *tf) {
+                                                 float2 *__restrict__ dst, const float2 *tc, const float2 *tf,
+                                                 bool discard = false) {
     static_assert(sizeof...(Rs) >= 1, "at least two passes");
-    dif_first_global<N, R1, T, H_SMEM>(src, x, tc, tf);
+    dif_first_global<N, R1, T, H_SMEM>(src, x, tc, tf, discard);
     filter_middle<N, N / R1, T, H_SMEM, Rs...>(x, h, hs, tc, tf);
     dit_last_global<N, R1, T>(x, dst, tc, tf);
 }

@@ -193,4 +193,8 @@ def test_batch_create_rejects_bad_arguments(lib):
     for il in (-1, 9):
         t = L.BatchTuningStruct(1024, 0, il, 0, -1)
         assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1   # interleave
+    t = L.BatchTuningStruct(1024, 0, 2, 0, -1, 33, 0)
+    assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1       # mix > 32
+    t = L.BatchTuningStruct(1024, 0, 2, 0, -1, 8, 1)
+    assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1       # unknown flag
     assert h.value is None

@@ -156,7 +156,10 @@ def test_batch_with_fft_plans_equals_image_fft(rosar):
         else:
             ref.append(rosar.image(s["raw"], s["win"], s["w"], s["o"]).cpu().numpy())
     assert sum("H" in s for s in scans) >= 3
-    for tuning in (rosar.Tuning(), rosar.Tuning(interleave=1, az_tile=512)):
+    D = rosar.batch.DISCARD_S
+    for tuning in (rosar.Tuning(), rosar.Tuning(interleave=1, az_tile=512), rosar.Tuning(interleave=2, mix=8, flags=D),
+                   rosar.Tuning(interleave=3, mix=32, flags=D), rosar.Tuning(interleave=2, mix=3),
+                   rosar.Tuning(interleave=0, flags=D)):
         b = rosar.Batch(scans, tuning)
         b.launch()
         b.status()
@@ -168,7 +171,10 @@ def test_batch_with_fft_plans_equals_image_fft(rosar):
     assert np.linalg.norm(ref[0] - orc) / np.linalg.norm(orc) < 1e-4
 
 
-def test_full_batched_workload_with_plans(rosar):
+@pytest.mark.parametrize("tuning", [dict(), dict(interleave=2, mix=8, flags=2), dict(interleave=3, mix=32, flags=2)])
+def test_full_batched_workload_with_plans(rosar, tuning):
+    """The 256-scan workload with whole-row FFT tiles in the tile orders and L2 options the autotuner times:
+    bit-exact vs rosar_image_fft, twice in a row (S dropped from L2 in the first launch is rewritten)."""
     import torch
     cfgs = synth.batched_configs()
     rng = np.random.default_rng(6)
@@ -182,10 +188,13 @@ def test_full_batched_workload_with_plans(rosar):
         w = torch.from_numpy(synth.default_weights(c, synth.draw_offsets(c))).cuda()
         scans.append({"raw": cubes[key].clone(), "w": w, "o": o, "H": rosar.azimuth_plan(w, o, c.n_az),
                       "win": torch.from_numpy(synth.hann_window(c.L)).cuda()})
-    b = rosar.Batch(scans)
-    b.launch()
-    b.status()
-    for i in range(0, len(scans), 23):
-        s = scans[i]
-        assert torch.equal(b.outs[i], rosar.image_fft(s["raw"], s["win"], s["H"])), i
+    b = rosar.Batch(scans, rosar.Tuning(**tuning))
+    refs = {i: rosar.image_fft(scans[i]["raw"], scans[i]["win"], scans[i]["H"]) for i in range(0, len(scans), 23)}
+    for _ in range(2):
+        for out in b.outs:
+            out.zero_()
+        b.launch()
+        b.status()
+        for i, r in refs.items():
+            assert torch.equal(b.outs[i], r), i
     b.close()
