@@ -873,6 +873,13 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
     t_k2m = timed(lambda i: rosar.sparse_azimuth_migrating(S_bufs[i % N_BUF], w, o, dl, out=outs[i % N_BUF]))
     t_mig_img = timed(lambda i: rosar.image_migrating(raws[i % N_BUF], win, w, o, dl, workspace=S_bufs[i % N_BUF],
                                                       out=outs[i % N_BUF]))
+    # the migrating filter in the frequency domain (planes per row offset of the taps)
+    mplan = rosar.azimuth_plan_migrating(w, o, dl, cfg.n_az)
+    ws_m = torch.empty((2, cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
+    t_migf_img = timed(lambda i: rosar.image_migrating_fft(raws[i % N_BUF], win, mplan, workspace=ws_m,
+                                                           out=outs[i % N_BUF]))
+    t_k2mf = timed(lambda i: rosar.sparse_azimuth_migrating_fft(S_bufs[i % N_BUF], mplan, spectrum=ws_m[1],
+                                                                out=outs[i % N_BUF]))
     K = cfg.K
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -896,6 +903,12 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
         "sparse_azimuth_mig_kernel": {"us_per_launch": t_k2m * 1e6, "algorithmic_flops": k2_flops,
                                       "tflops": k2_flops / t_k2m / 1e12,
                                       "alu_frac": k2_flops / t_k2m / 1e12 / fp32_peak},
+        "migrating filter, frequency domain (2 launches)": {
+            "us_per_call": t_k2mf * 1e6, "planes": mplan.n_d,
+            "algorithmic_bytes": (16.0 + 8.0 * (1 + 2 * mplan.n_d)) * px,
+            "hbm_frac": (16.0 + 8.0 * (1 + 2 * mplan.n_d)) * px / t_k2mf / 1e9 / hbm,
+            "note": "spectrum of every S row (S in, X out) + per row the planes' products and the inverse (n_d rows "
+                    "of X and of H in, image out)"},
         "azimuth_fft_fixed_kernel<256, 3600, 16, 15, 15>": {
             "us_per_launch": t_k2f * 1e6, "algorithmic_bytes": k2f_bytes, "gbs": k2f_bytes / t_k2f / 1e9,
             "hbm_frac": k2f_bytes / t_k2f / 1e9 / hbm,
@@ -909,7 +922,8 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
            "px_s": value, "ms_per_scan": ms / steps, "scans_timed": steps,
            "timed_path": "rosar_image_fft_scans (16 scans per call, graph replays)" if pipelined else "rosar_image_fft",
            "autotune": choice, "kernels": kernels,
-           "image_gather_px_s": world * px / t_gather_img, "image_migrating_px_s": world * px / t_mig_img}
+           "image_gather_px_s": world * px / t_gather_img, "image_migrating_px_s": world * px / t_mig_img,
+           "image_migrating_fft_px_s": world * px / t_migf_img}
     if pipelined:
         def call_ms(n, reps_=64):
             m_, _ = graph_loop(torch, lambda i: scans_call(n), reps_, 3, 1, stream, world, device)
@@ -966,7 +980,7 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
                                   "tensor_frac": 3 * f_st / t_st / 1e12 / bf16_peak,
                                   "traffic": recorded_traffic("td_tc_kernel<0>", "indoor", source_hash("time_domain.cu"))},
             "paper_table_ms_per_image": {"BPA": t_bt * 1e3, "SAS": t_st * 1e3, "FFT+BPA": (t_bn + t_k1) * 1e3,
-                                         "FFT+SAS": ms / steps},
+                                         "FFT+SAS": ms / steps, "FFT+SAS (per-pulse peak bins)": t_migf_img * 1e3},
             "note": "FFT+BPA = range compression + back-projection over M=600 pulses (bpa_kernel<1>: supplied "
                     "rotation errors, per pixel-pulse geometry; <0>: nominal); BPA / SAS = time-domain forms "
                     "(Eq. (14); Algorithm 2 with W_SA) on the tensor cores, tensor_frac of the measured sustained "

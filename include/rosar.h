@@ -284,6 +284,45 @@ ROSAR_API rosar_status rosar_image_fft_scans(const rosar_c32 *raw, const float *
 /* 1 if rosar_image_fft_scans overlaps consecutive scans for this (L, n_az), else 0. */
 ROSAR_API int rosar_image_fft_scans_pipelined(int L, int n_az);
 
+/*
+ * The range-migration-aware filter of rosar_sparse_azimuth_migrating (Sec. III-D: each pulse's
+ * peak bin l*_n of Eq. (40) inside Eq. (43)) in the azimuth-frequency domain.  Grouping row
+ * r's taps by their row offset d = dl[r][k],
+ *   out[r][.] = sum_d IFFT(H_d[r] * FFT(S[r+d][.])),   H_d[r] = FFT(g_{r,d}) / n_az,
+ *   g_{r,d}[(-o_k) mod n_az] += w[r][k] over the taps with dl[r][k] = d,
+ * rows r+d outside 0 .. n_bins-1 contributing nothing: the same sums as the gather form up
+ * to float32 rounding, at the cost of the fixed-row FFT filter plus one product per plane.
+ *
+ * rosar_azimuth_plan_migrating: the n_d planes d = d_lo .. d_lo+n_d-1 of the weight design.
+ *   w, o, o_row_stride, n_rng, n_az, K: as rosar_azimuth_plan                  (in)
+ *   dl   [n_rng][K] int32 row offsets; taps whose dl lies outside [d_lo, d_lo+n_d) are in
+ *        no plane, so the caller passes the full range of dl                    (in)
+ *   H    [n_d][n_rng][n_az] complex, an opaque table as rosar_azimuth_plan's    (out)
+ * Limits: 1 <= n_d <= 16; ROSAR_ERR_UNSUPPORTED if rosar_azimuth_fft_supported(n_az) is 0.
+ */
+ROSAR_API rosar_status rosar_azimuth_plan_migrating(const rosar_c32 *w, const int32_t *o, int o_row_stride,
+                                                    const int32_t *dl, int d_lo, int n_d, int n_rng, int n_az, int K,
+                                                    rosar_c32 *H, void *stream);
+
+/*
+ *   S         [n_bins][n_az] complex range-compressed rows (in)
+ *   H         [n_d][n_rng][n_az] from rosar_azimuth_plan_migrating with the same d_lo, n_d (in)
+ *   spectrum  [n_bins][n_az] complex: the rows' forward transforms              (scratch)
+ *   out       [n_rng][n_az] complex image                                       (out)
+ * Two launches: the forward transform of every row of S, then per output row the planes'
+ * products and the inverse.  out and spectrum must not overlap S, H or each other.
+ */
+ROSAR_API rosar_status rosar_sparse_azimuth_migrating_fft(const rosar_c32 *S, int n_bins, const rosar_c32 *H, int d_lo,
+                                                          int n_d, int n_rng, int n_az, rosar_c32 *spectrum,
+                                                          rosar_c32 *out, void *stream);
+
+/* rosar_image_migrating with the frequency-domain filter: range compression into workspace[0],
+ * then rosar_sparse_azimuth_migrating_fft over the L rows with spectrum = workspace[1].
+ *   workspace [2][L][n_az] complex (scratch); other arguments as above with n_bins = n_rng = L. */
+ROSAR_API rosar_status rosar_image_migrating_fft(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int d_lo,
+                                                 int n_d, int n_az, int L, rosar_c32 *workspace, rosar_c32 *out,
+                                                 void *stream);
+
 /* ------------------------------------------------------------------------
  * Differentiable form: a stack of n_scans scans [n_scans][n_rng][n_az] that share
  * one weight set, a per-pulse phase correction eps [n_scans][n_az] applied to the

@@ -12,6 +12,8 @@ from .ops import azimuth_weight_grad_fft, bpa_time, image_fft_host, sas_time, sp
 from .ops import image_fft_scans, image_fft_scans_pipelined, image_l2_loss, image_l2_loss_grad  # noqa: F401
 from .ops import (image_migrating, phase_apply, phase_grad, range_compress_adjoint,  # noqa: F401
                   sparse_azimuth_adjoint, sparse_azimuth_migrating, sparse_azimuth_scans)
+from .ops import (MigratingPlan, azimuth_plan_migrating, image_migrating_fft,  # noqa: F401
+                  sparse_azimuth_migrating_fft)
 from .batch import Batch, Tuning  # noqa: F401
 from . import autograd, autotune  # noqa: F401
 

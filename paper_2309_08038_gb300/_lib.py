@@ -63,6 +63,9 @@ _PROTOS = {
     "rosar_image_migrating": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_azimuth_fft_supported": (_I, [_I]),
     "rosar_azimuth_plan": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_azimuth_plan_migrating": (_I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "rosar_sparse_azimuth_migrating_fft": (_I, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_image_migrating_fft": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_sparse_azimuth_fft": (_I, [_P, _P, _I, _I, _P, _P]),
     "rosar_image_fft": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "rosar_image_fft_scans": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),

@@ -121,19 +121,25 @@ azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict_
     filter_row_cta<T, N, stage_h_fits<N>(), R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm);
 }
 
+// dl != nullptr: plane blockIdx.y of the range-migration-aware plan, built from the taps of row r whose row
+// offset dl[r][k] equals d_lo + blockIdx.y, stored at H[(blockIdx.y * gridDim.x + r) * N].
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT == 384 ? 2 : 1))
 azimuth_plan_kernel(const float2 *__restrict__ w, const int32_t *__restrict__ o, int o_row_stride, int K, int N,
-                    RowPlan pl, Layout lay, float2 *__restrict__ H) {
+                    RowPlan pl, Layout lay, float2 *__restrict__ H, const int32_t *__restrict__ dl = nullptr,
+                    int d_lo = 0) {
     extern __shared__ float2 sm[];
     float2 *x = sm;
     float2 *tw = x + padded_len(N);
     const int r = blockIdx.x;
+    const int d_sel = d_lo + (int)blockIdx.y;
+    H += (size_t)blockIdx.y * gridDim.x * N;
     const float2 *tc, *tf;
     build_twiddles(N, lay.full_tab != 0, tw, &tc, &tf);
     for (int n = threadIdx.x; n < padded_len(N); n += blockDim.x) x[n] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {        // g_r[(-o_k) mod N] += w[r][k]
+        if (dl && __ldg(dl + (size_t)r * K + k) != d_sel) continue;
         const long long on = -(long long)__ldg(o + (size_t)r * o_row_stride + k);
         const int n = (int)(((on % N) + N) % N);
         const float2 wv = __ldg(w + (size_t)r * K + k);
@@ -466,7 +472,7 @@ rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, 
 }
 
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
-                                 float2 *H, cudaStream_t s) {
+                                 float2 *H, cudaStream_t s, const int32_t *dl, int d_lo, int n_d) {
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_plan: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
@@ -474,12 +480,13 @@ rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_st
     const Layout lay = layout_for(n_az, false);
     static const void *const ks[4] = {(const void *)azimuth_plan_kernel<256>, (const void *)azimuth_plan_kernel<384>,
                                       (const void *)azimuth_plan_kernel<512>, (const void *)azimuth_plan_kernel<1024>};
+    const dim3 grid(n_rng, dl ? n_d : 1);
     return launch_rows(
         n_az, n_rng, lay.bytes,
-        [&](int g, int t, size_t sm) { azimuth_plan_kernel<256><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
-        [&](int g, int t, size_t sm) { azimuth_plan_kernel<384><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
-        [&](int g, int t, size_t sm) { azimuth_plan_kernel<512><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
-        [&](int g, int t, size_t sm) { azimuth_plan_kernel<1024><<<g, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H); },
+        [&](int, int t, size_t sm) { azimuth_plan_kernel<256><<<grid, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H, dl, d_lo); },
+        [&](int, int t, size_t sm) { azimuth_plan_kernel<384><<<grid, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H, dl, d_lo); },
+        [&](int, int t, size_t sm) { azimuth_plan_kernel<512><<<grid, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H, dl, d_lo); },
+        [&](int, int t, size_t sm) { azimuth_plan_kernel<1024><<<grid, t, sm, s>>>(w, o, o_row_stride, K, n_az, pl, lay, H, dl, d_lo); },
         ks, done, "azimuth_plan");
 }
 

@@ -274,6 +274,76 @@ rosar_status rosar_azimuth_plan(const rosar_c32 *w, const int32_t *o, int o_row_
                                reinterpret_cast<float2 *>(H), static_cast<cudaStream_t>(stream));
 }
 
+rosar_status rosar_azimuth_plan_migrating(const rosar_c32 *w, const int32_t *o, int o_row_stride, const int32_t *dl,
+                                          int d_lo, int n_d, int n_rng, int n_az, int K, rosar_c32 *H, void *stream) {
+    clear_error();
+    if (!w || !o || !dl || !H) return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan_migrating: null pointer argument");
+    if (n_rng < 1 || n_az < 1 || K < 1 || (o_row_stride != 0 && o_row_stride < K) || n_d < 1 || n_d > 16)
+        return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan_migrating: n_rng=%d n_az=%d K=%d o_row_stride=%d n_d=%d",
+                         n_rng, n_az, K, o_row_stride, n_d);
+    if ((long long)n_d * n_rng * n_az > kMaxElems || (long long)n_rng * K > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_plan_migrating: H too large");
+    if (misaligned(w, 8) || misaligned(o, 4) || misaligned(dl, 4) || misaligned(H, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan_migrating: misaligned pointer");
+    const size_t hb = sizeof(rosar_c32) * (size_t)n_d * n_rng * n_az;
+    if (overlaps(H, hb, w, sizeof(rosar_c32) * (size_t)n_rng * K) || overlaps(H, hb, dl, sizeof(int32_t) * (size_t)n_rng * K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "azimuth_plan_migrating: H overlaps an input");
+    return launch_azimuth_plan(reinterpret_cast<const float2 *>(w), o, o_row_stride, n_rng, n_az, K,
+                               reinterpret_cast<float2 *>(H), static_cast<cudaStream_t>(stream), dl, d_lo, n_d);
+}
+
+namespace {
+rosar_status check_migrating_fft(const void *S, int n_bins, const void *H, int n_d, int n_rng, int n_az,
+                                 const void *spectrum, const void *out, const char *what) {
+    if (!S || !H || !spectrum || !out) return set_error(ROSAR_ERR_INVALID_ARG, "%s: null pointer argument", what);
+    if (n_bins < 1 || n_rng < 1 || n_az < 1 || n_d < 1 || n_d > 16)
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: n_bins=%d n_rng=%d n_az=%d n_d=%d", what, n_bins, n_rng, n_az, n_d);
+    if ((long long)n_bins * n_az > kMaxElems || (long long)n_d * n_rng * n_az > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: array too large", what);
+    if (misaligned(S, 8) || misaligned(H, 8) || misaligned(spectrum, 8) || misaligned(out, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: misaligned pointer", what);
+    const size_t sb = sizeof(rosar_c32) * (size_t)n_bins * n_az, ob = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    const size_t hb = sizeof(rosar_c32) * (size_t)n_d * n_rng * n_az;
+    if (overlaps(out, ob, S, sb) || overlaps(out, ob, H, hb) || overlaps(out, ob, spectrum, sb) ||
+        overlaps(spectrum, sb, S, sb) || overlaps(spectrum, sb, H, hb))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: out or spectrum overlaps another argument", what);
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: n_az=%d is not 2^a 3^b 5^c <= 16384", what, n_az);
+    return ROSAR_OK;
+}
+}  // namespace
+
+rosar_status rosar_sparse_azimuth_migrating_fft(const rosar_c32 *S, int n_bins, const rosar_c32 *H, int d_lo, int n_d,
+                                                int n_rng, int n_az, rosar_c32 *spectrum, rosar_c32 *out,
+                                                void *stream) {
+    clear_error();
+    rosar_status st = check_migrating_fft(S, n_bins, H, n_d, n_rng, n_az, spectrum, out, "sparse_azimuth_migrating_fft");
+    if (st != ROSAR_OK) return st;
+    return launch_sparse_azimuth_migrating_fft(reinterpret_cast<const float2 *>(S), n_bins,
+                                               reinterpret_cast<const float2 *>(H), d_lo, n_d, n_rng, n_az,
+                                               reinterpret_cast<float2 *>(spectrum), reinterpret_cast<float2 *>(out),
+                                               static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_image_migrating_fft(const rosar_c32 *raw, const float *win, const rosar_c32 *H, int d_lo, int n_d,
+                                       int n_az, int L, rosar_c32 *workspace, rosar_c32 *out, void *stream) {
+    clear_error();
+    rosar_status st = check_range_args(raw, win, n_az, L, workspace);
+    if (st != ROSAR_OK) return st;
+    rosar_c32 *S = workspace, *X = workspace + (size_t)n_az * L;
+    st = check_migrating_fft(S, L, H, n_d, L, n_az, X, out, "image_migrating_fft");
+    if (st != ROSAR_OK) return st;
+    const size_t bytes = sizeof(rosar_c32) * (size_t)n_az * L;
+    if (overlaps(raw, bytes, out, bytes) || overlaps(raw, bytes, workspace, 2 * bytes))
+        return set_error(ROSAR_ERR_INVALID_ARG, "image_migrating_fft: raw overlaps out or the workspace");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = launch_range_compress(reinterpret_cast<const float2 *>(raw), win, n_az, L, 1, reinterpret_cast<float2 *>(S), s);
+    if (st != ROSAR_OK) return st;
+    return launch_sparse_azimuth_migrating_fft(reinterpret_cast<const float2 *>(S), L, reinterpret_cast<const float2 *>(H),
+                                               d_lo, n_d, L, n_az, reinterpret_cast<float2 *>(X),
+                                               reinterpret_cast<float2 *>(out), s);
+}
+
 rosar_status rosar_sparse_azimuth_fft(const rosar_c32 *S, const rosar_c32 *H, int n_rng, int n_az, rosar_c32 *out,
                                       void *stream) {
     clear_error();

@@ -112,8 +112,13 @@ rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int
 // grad_w[r][k] = sum_s sum_t g[s][r][t] conj(S_t[s][r][(t + o_k) mod n_az]) from the per-row cross-spectrum.
 rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
                                             int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s);
+// dl != nullptr: the n_d planes of the range-migration-aware plan, plane i from the taps with dl = d_lo + i,
+// H [n_d][n_rng][n_az].
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,
-                                 float2 *H, cudaStream_t s);
+                                 float2 *H, cudaStream_t s, const int32_t *dl = nullptr, int d_lo = 0, int n_d = 1);
+// Range-migration-aware filter in the frequency domain (azimuth_mig_fft.cu): X [n_bins][n_az] scratch.
+rosar_status launch_sparse_azimuth_migrating_fft(const float2 *S, int n_bins, const float2 *H, int d_lo, int n_d,
+                                                 int n_rng, int n_az, float2 *X, float2 *out, cudaStream_t s);
 
 struct BpaParams {
     float inv_dR;        // 1/dR, bins per metre

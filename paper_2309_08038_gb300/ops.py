@@ -462,3 +462,66 @@ def image_migrating(raw, win, w, o, dl, workspace=None, out=None, stream=None):
     check(lib.rosar_image_migrating(ptr(raw), ptr(win), ptr(w), ptr(o), stride, ptr(dl), n_az, L, K, ptr(workspace),
                                     ptr(out), stream_handle(stream)))
     return out
+
+
+@dataclass(frozen=True)
+class MigratingPlan:
+    """The planes of rosar_azimuth_plan_migrating: H [n_d, n_rng, n_az] for row offsets d_lo .. d_lo + n_d - 1."""
+
+    H: torch.Tensor
+    d_lo: int
+    n_d: int
+
+
+def azimuth_plan_migrating(w, o, dl, n_az, stream=None):
+    """rosar_azimuth_plan_migrating: the frequency-domain planes of the range-migration-aware taps (w [n_rng, K],
+    offsets o, row offsets dl [n_rng, K]); the planes span the full range of dl (read once on the host)."""
+    lib = _lib.load()
+    require(w, torch.complex64, "w", ndim=2)
+    n_rng, K = w.shape
+    stride = _offsets(o, n_rng, K)
+    require(dl, torch.int32, "dl", shape=(n_rng, K))
+    d_lo, d_hi = int(dl.min().item()), int(dl.max().item())
+    n_d = d_hi - d_lo + 1
+    H = torch.empty((n_d, n_rng, n_az), dtype=torch.complex64, device=w.device)
+    check(lib.rosar_azimuth_plan_migrating(ptr(w), ptr(o), stride, ptr(dl), d_lo, n_d, n_rng, n_az, K, ptr(H),
+                                           stream_handle(stream)))
+    return MigratingPlan(H, d_lo, n_d)
+
+
+def sparse_azimuth_migrating_fft(S, plan: MigratingPlan, spectrum=None, out=None, stream=None):
+    """rosar_sparse_azimuth_migrating_fft: the range-migration-aware filter of S [n_bins, n_az] through its planes."""
+    lib = _lib.load()
+    require(S, torch.complex64, "S", ndim=2)
+    n_bins, n_az = S.shape
+    n_d, n_rng = plan.H.shape[0], plan.H.shape[1]
+    require(plan.H, torch.complex64, "H", shape=(n_d, n_rng, n_az))
+    if spectrum is None:
+        spectrum = torch.empty_like(S)
+    if out is None:
+        out = torch.empty((n_rng, n_az), dtype=torch.complex64, device=S.device)
+    require(spectrum, torch.complex64, "spectrum", shape=(n_bins, n_az))
+    require(out, torch.complex64, "out", shape=(n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_migrating_fft(ptr(S), n_bins, ptr(plan.H), plan.d_lo, plan.n_d, n_rng, n_az,
+                                                 ptr(spectrum), ptr(out), stream_handle(stream)))
+    return out
+
+
+def image_migrating_fft(raw, win, plan: MigratingPlan, workspace=None, out=None, stream=None):
+    """rosar_image_migrating_fft: range compression, then the migration-aware filter in the frequency domain;
+    workspace [2, L, n_az]."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", ndim=2)
+    n_az, L = raw.shape
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    require(plan.H, torch.complex64, "H", shape=(plan.n_d, L, n_az))
+    if workspace is None:
+        workspace = torch.empty((2, L, n_az), dtype=torch.complex64, device=raw.device)
+    if out is None:
+        out = torch.empty((L, n_az), dtype=torch.complex64, device=raw.device)
+    require(workspace, torch.complex64, "workspace", shape=(2, L, n_az))
+    require(out, torch.complex64, "out", shape=(L, n_az))
+    check(lib.rosar_image_migrating_fft(ptr(raw), ptr(win), ptr(plan.H), plan.d_lo, plan.n_d, n_az, L, ptr(workspace),
+                                        ptr(out), stream_handle(stream)))
+    return out

@@ -198,3 +198,19 @@ def test_batch_create_rejects_bad_arguments(lib):
     t = L.BatchTuningStruct(1024, 0, 2, 0, -1, 8, 1)
     assert lib.rosar_batch_create(scans, 2, ctypes.byref(t), ws, n, ctypes.byref(h)) == 1       # unknown flag
     assert h.value is None
+
+
+def test_migrating_fft_rejects_bad_arguments(lib):
+    FAKE3, FAKE4 = ctypes.c_void_p(0x30000000), ctypes.c_void_p(0x40000000)
+    p = lib.rosar_azimuth_plan_migrating
+    assert p(FAKE, FAKE2, 0, None, 0, 2, 4, 3600, 8, FAKE3, None) == 1            # null dl
+    assert p(FAKE, FAKE2, 0, FAKE4, 0, 17, 4, 3600, 8, FAKE3, None) == 1          # n_d > 16
+    assert p(FAKE, FAKE2, 0, FAKE4, 0, 0, 4, 3600, 8, FAKE3, None) == 1           # n_d < 1
+    assert p(FAKE, FAKE2, 0, FAKE4, 0, 2, 4, 1031, 8, FAKE3, None) == 2           # 1031 has no FFT plan
+    f = lib.rosar_sparse_azimuth_migrating_fft
+    assert f(FAKE, 8, FAKE2, 0, 2, 8, 3600, None, FAKE4, None) == 1               # null spectrum
+    assert f(FAKE, 8, FAKE2, 0, 2, 8, 3600, FAKE, FAKE4, None) == 1               # spectrum aliases S
+    assert f(FAKE, 8, FAKE2, 0, 2, 8, 1031, FAKE3, FAKE4, None) == 2              # no FFT plan
+    assert b"1031" in lib.rosar_last_error()
+    g = lib.rosar_image_migrating_fft
+    assert g(FAKE, None, FAKE2, 0, 2, 3600, 48, FAKE3, FAKE4, None) == 2          # L not a power of two
