@@ -989,18 +989,20 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
     return res, indoor_img, (cfg, sc, w, o, win)
 
 
-def diff_bytes_per_px(n_scans, fused_phase):
+def diff_bytes_per_px(n_scans, fused_phase, spectra, with_grad):
     """Algorithmic bytes per image pixel of the differentiable step's kernels (frequency-domain form): each
     kernel's inputs read once and outputs written once; the plan H (one per step, shared by the scans) counts
-    once per step.  fused_phase: the phase correction is applied inside the filter and the gradient kernels
-    (no S~ = S e^{j eps} stack in memory)."""
+    once per step.  fused_phase: the phase correction is applied as the kernels load S (no S~ = S e^{j eps}
+    stack in memory); spectra: the forward and adjoint filters store their rows' transforms (8 B/px each) and
+    the weight gradient reads those two (16 B/px) instead of transforming g and S~ again."""
     plan = 8.0 / n_scans
     fwd = [("range_compress_kernel (stack)", 16.0), ("azimuth_plan_kernel", plan)]
     if not fused_phase:
         fwd.append(("phase_apply_kernel", 16.0))
-    fwd.append(("azimuth filter (H)", 16.0 + plan))
-    bwd = [("loss_partial_kernel", 16.0), ("loss_grad_kernel", 24.0), ("adjoint filter (conj H)", 16.0 + plan),
-           ("azimuth_xspec (weight gradient)", 16.0), ("phase_grad_kernel", 16.0)]
+    fwd.append(("azimuth filter (H)", 16.0 + plan + (8.0 if (spectra and with_grad) else 0.0)))
+    bwd = [("loss_partial_kernel", 16.0), ("loss_grad_kernel", 24.0),
+           ("adjoint filter (conj H)", 16.0 + plan + (8.0 if spectra else 0.0)),
+           ("weight gradient (cross-spectrum)", 16.0), ("phase_grad_kernel", 16.0)]
     return fwd, bwd
 
 
@@ -1046,13 +1048,37 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, hbm,
         ms_b, _ = time_loop(torch, fwd_bwd, n, 3, stream, world, device)
         return ms_f / n * 1e-3, ms_b / n * 1e-3
 
+    def graphed_step_time(method, n=20):
+        """The same forward + loss + backward captured once in a CUDA graph and replayed: the kernels the eager
+        step launches, without the host's per-launch and autograd work between them."""
+        side = torch.cuda.Stream(device=device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                wp.grad = None
+                eps.grad = None
+                rosar.autograd.image_l2_loss(forward(method), Bref).backward()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        wp.grad = None
+        eps.grad = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            rosar.autograd.image_l2_loss(forward(method), Bref).backward()
+        torch.cuda.synchronize()
+        ms, _ = time_loop(torch, lambda i: g.replay(), n, 3, stream, world, device)
+        return ms / n * 1e-3
+
     t_f, t_b = timings("auto")
+    t_bgr = graphed_step_time("auto")
     t_fg, t_bg = timings("gather")
     pix = n_scans * px
     fused = bool(getattr(rosar.autograd, "FUSED_PHASE", False))
-    fwd_b, bwd_b = diff_bytes_per_px(n_scans, fused)
+    spectra = bool(getattr(rosar.autograd, "SPECTRA", False))
+    fwd_b, _ = diff_bytes_per_px(n_scans, fused, spectra, False)
+    fwd_g, bwd_b = diff_bytes_per_px(n_scans, fused, spectra, True)
     bf = sum(b for _, b in fwd_b)
-    bb = bf + sum(b for _, b in bwd_b)
+    bb = sum(b for _, b in fwd_g) + sum(b for _, b in bwd_b)
 
     def roof(bpp, t):
         return {"bound": "hbm", "achieved": bpp * pix / t / 1e9, "peak": hbm, "unit": "GB/s",
@@ -1060,14 +1086,17 @@ def diff_bench(torch, rosar, cfg, sc, w, o, win, stream, world, device, px, hbm,
                 "peak_note": f"HBM copy bandwidth of {peak_src} peaks"}
     return {"scans": n_scans, "pixels": pix, "fwd_px_s": world * pix / t_f, "fwd_bwd_px_s": world * pix / t_b,
             "ms_fwd": t_f * 1e3, "ms_fwd_bwd": t_b * 1e3, "bwd_over_fwd": (t_b - t_f) / t_f,
-            "roofline_fwd": roof(bf, t_f), "roofline_fwd_bwd": roof(bb, t_b),
-            "bytes_accounting": {"forward": fwd_b, "backward": bwd_b, "phase_fused": fused},
+            "ms_fwd_bwd_graph": t_bgr * 1e3, "fwd_bwd_graph_px_s": world * pix / t_bgr,
+            "roofline_fwd": roof(bf, t_f), "roofline_fwd_bwd": roof(bb, t_b), "roofline_fwd_bwd_graph": roof(bb, t_bgr),
+            "bytes_accounting": {"forward": fwd_b, "forward_with_grad": fwd_g, "backward": bwd_b, "phase_fused": fused,
+                                 "spectra_stored": spectra},
             "gather_fwd_px_s": world * pix / t_fg, "gather_fwd_bwd_px_s": world * pix / t_bg,
             "grad_finite": bool(torch.isfinite(wp.grad).all().item() and torch.isfinite(eps.grad).all().item()),
             "note": "step = range compression of the 16 scans (one launch) + phase correction + sparse azimuth filter "
                     "(forward), loss ||image - BPA image||^2 (rosar_image_l2_loss), adjoint filter + weight "
                     "gradient + phase gradient (backward); default = frequency-domain kernels (plan from w each "
-                    "step, filter with H / conj(H), cross-spectrum weight gradient), gather_* = the gather kernels"}
+                    "step, filter with H / conj(H), cross-spectrum weight gradient), gather_* = the gather kernels; "
+                    "*_graph = the same step captured in one CUDA graph and replayed (no host work between kernels)"}
 
 
 def tiny_image(torch, rosar, device):

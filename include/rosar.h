@@ -388,6 +388,36 @@ ROSAR_API rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *g
                                         void *stream);
 
 /*
+ * The same step without the corrected copy S_t in memory: the phase factors P = exp(j*eps) are computed once
+ * per (scan, pulse) and every kernel that reads S_t forms S * P as it loads S (same products, same results as
+ * rosar_phase_apply followed by the calls above).
+ *   rosar_phasors:        P[i] = exp(j*eps[i]) for i < n (eps float, P complex; n = n_scans * n_az).
+ *   rosar_sparse_azimuth_fft_scans_ex: rosar_sparse_azimuth_fft_scans of S * P (P NULL: of S), and (spectrum
+ *                         not NULL) the rows' forward transforms written to spectrum [n_scans][n_rng][n_az] in an
+ *                         internal order (fixed per n_az), before the product with H or conj(H).
+ *   rosar_azimuth_weight_grad_fft_phase: rosar_azimuth_weight_grad_fft with S_t = S * P.
+ *   rosar_azimuth_weight_grad_spectra: the same gradient from stored transforms: G = the spectrum of the
+ *                         adjoint call (g), X = the spectrum of the forward call (S * P); the cross-spectrum
+ *                         sum_s G_s conj(X_s) (scan order) into workspace [n_rng][n_az] (scratch), then per row
+ *                         one inverse transform: no forward transform repeated.
+ *   rosar_phase_grad_phasor: rosar_phase_grad with S_t = S * P and grad_S = grad_S_t * conj(P).
+ *   S [n_scans][n_rng][n_az], P [n_scans][n_az] (in); other arguments and limits as the calls above.
+ */
+ROSAR_API rosar_status rosar_phasors(const float *eps, long long n, rosar_c32 *P, void *stream);
+ROSAR_API rosar_status rosar_sparse_azimuth_fft_scans_ex(const rosar_c32 *S, const rosar_c32 *P, const rosar_c32 *H,
+                                                         int n_scans, int n_rng, int n_az, int adjoint, rosar_c32 *out,
+                                                         rosar_c32 *spectrum, void *stream);
+ROSAR_API rosar_status rosar_azimuth_weight_grad_fft_phase(const rosar_c32 *g, const rosar_c32 *S, const rosar_c32 *P,
+                                                           const int32_t *o, int o_row_stride, int n_scans, int n_rng,
+                                                           int n_az, int K, rosar_c32 *grad_w, void *stream);
+ROSAR_API rosar_status rosar_azimuth_weight_grad_spectra(const rosar_c32 *G, const rosar_c32 *X, const int32_t *o,
+                                                         int o_row_stride, int n_scans, int n_rng, int n_az, int K,
+                                                         rosar_c32 *workspace, rosar_c32 *grad_w, void *stream);
+ROSAR_API rosar_status rosar_phase_grad_phasor(const rosar_c32 *S, const rosar_c32 *P, const rosar_c32 *grad_S_t,
+                                               int n_scans, int n_rng, int n_az, float *grad_eps, rosar_c32 *grad_S,
+                                               void *stream);
+
+/*
  * Image loss of the differentiable form: the squared L2 distance between an image stack and a reference
  * stack (e.g. back-projection images of the same scans), and its gradient in the same convention:
  *   loss    = sum_{i<n} |out[i] - ref[i]|^2                       (rosar_image_l2_loss)

@@ -14,6 +14,8 @@ from .ops import (image_migrating, phase_apply, phase_grad, range_compress_adjoi
                   sparse_azimuth_adjoint, sparse_azimuth_migrating, sparse_azimuth_scans)
 from .ops import (MigratingPlan, azimuth_plan_migrating, image_migrating_fft,  # noqa: F401
                   sparse_azimuth_migrating_fft)
+from .ops import (azimuth_weight_grad_fft_phase, azimuth_weight_grad_spectra, phase_grad_phasor,  # noqa: F401
+                  phasors, sparse_azimuth_fft_scans_ex)
 from .batch import Batch, Tuning  # noqa: F401
 from . import autograd, autotune  # noqa: F401
 

@@ -63,6 +63,11 @@ _PROTOS = {
     "rosar_image_migrating": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_azimuth_fft_supported": (_I, [_I]),
     "rosar_azimuth_plan": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_phasors": (_I, [_P, ctypes.c_longlong, _P, _P]),
+    "rosar_sparse_azimuth_fft_scans_ex": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_azimuth_weight_grad_spectra": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "rosar_azimuth_weight_grad_fft_phase": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "rosar_phase_grad_phasor": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_azimuth_plan_migrating": (_I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     "rosar_sparse_azimuth_migrating_fft": (_I, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P]),
     "rosar_image_migrating_fft": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),

@@ -17,39 +17,56 @@ import torch
 from . import ops
 
 
+# The frequency-domain form keeps no phase-corrected copy S_t = S exp(j eps) in memory: the phase factors are
+# computed once per (scan, pulse) and applied as the filter and the phase gradient load S.  When the weights
+# need a gradient, the forward filter and the adjoint filter also store their rows' transforms, and the weight
+# gradient is one inverse transform per row of their cross-spectrum.
+FUSED_PHASE = True
+SPECTRA = True
+
+
 class SparseAzimuthPhase(torch.autograd.Function):
-    """method "gather": the gather kernels (rosar_sparse_azimuth_scans / _adjoint); "fft": the frequency-domain
-    forms (plan H from w every forward, filter and adjoint filter with H and conj(H), weight gradient from the
-    per-row cross-spectrum).  Both compute the same sums; "auto" picks "fft" where the row length allows it."""
+    """method "gather": the gather kernels (rosar_sparse_azimuth_scans / _adjoint) on S_t = S exp(j eps) from
+    rosar_phase_apply; "fft": the frequency-domain forms (plan H from w every forward, filter and adjoint filter with
+    H and conj(H), weight gradient from the per-row cross-spectrum), each forming S exp(j eps) as it loads S.  Both
+    compute the same sums; "auto" picks "fft" where the row length allows it."""
 
     @staticmethod
-    def forward(ctx, S, eps, w, o, method):
-        S_t = ops.phase_apply(S.contiguous(), eps.contiguous())
+    def forward(ctx, S, eps, w, o, method, keep_spectra):
+        S = S.contiguous()
         w = w.contiguous()
-        H = None
-        if method == "fft":
-            H = ops.azimuth_plan(w, o, S.shape[2])
-            out = ops.sparse_azimuth_fft_scans(S_t, H)
-        else:
-            out = ops.sparse_azimuth_scans(S_t, w, o)
         ctx.method = method
-        ctx.save_for_backward(S_t, eps, w, o, H)
+        if method == "fft":
+            P = ops.phasors(eps.contiguous())
+            H = ops.azimuth_plan(w, o, S.shape[2])
+            X = torch.empty_like(S) if (keep_spectra and ctx.needs_input_grad[2]) else None
+            out = ops.sparse_azimuth_fft_scans_ex(S, H, P=P, spectrum=X)
+            ctx.save_for_backward(S, P, w, o, H, X)
+        else:
+            S_t = ops.phase_apply(S, eps.contiguous())
+            out = ops.sparse_azimuth_scans(S_t, w, o)
+            ctx.save_for_backward(S_t, eps, w, o)
         return out
 
     @staticmethod
     def backward(ctx, g):
-        S_t, eps, w, o, H = ctx.saved_tensors
         need_S, need_eps, need_w = ctx.needs_input_grad[:3]
         g = g.contiguous()
+        grad_eps = grad_S = grad_w = None
         if ctx.method == "fft":
-            grad_S_t = ops.sparse_azimuth_fft_scans(g, H, adjoint=True) if (need_S or need_eps) else None
-            grad_w = ops.azimuth_weight_grad_fft(g, S_t, o, w.shape[1]) if need_w else None
+            S, P, w, o, H, X = ctx.saved_tensors
+            G = torch.empty_like(g) if need_w else None
+            grad_S_t = ops.sparse_azimuth_fft_scans_ex(g, H, adjoint=True, spectrum=G) if (need_S or need_eps or need_w) \
+                else None
+            grad_w = ops.azimuth_weight_grad_spectra(G, X, o, w.shape[1]) if need_w else None
+            if need_S or need_eps:
+                grad_eps, grad_S = ops.phase_grad_phasor(S, P, grad_S_t, want_eps=need_eps, want_S=need_S)
         else:
+            S_t, eps, w, o = ctx.saved_tensors
             grad_S_t, grad_w = ops.sparse_azimuth_adjoint(g, S_t, w, o, want_S=need_S or need_eps, want_w=need_w)
-        grad_eps = grad_S = None
-        if need_S or need_eps:
-            grad_eps, grad_S = ops.phase_grad(S_t, grad_S_t, eps.contiguous(), want_eps=need_eps, want_S=need_S)
-        return grad_S, grad_eps, grad_w, None, None
+            if need_S or need_eps:
+                grad_eps, grad_S = ops.phase_grad(S_t, grad_S_t, eps.contiguous(), want_eps=need_eps, want_S=need_S)
+        return grad_S, grad_eps, grad_w, None, None, None
 
 
 class RangeCompress(torch.autograd.Function):
@@ -98,7 +115,8 @@ def sparse_azimuth_phase(S, eps, w, o, method="auto"):
         method = "fft" if (ops.azimuth_fft_supported(n_az) and n_az <= _FFT_MAX_N_AZ) else "gather"
     if method not in ("fft", "gather"):
         raise ValueError("method must be 'auto', 'fft' or 'gather'")
-    return SparseAzimuthPhase.apply(S, eps, w, o, method)
+    # the forward filter keeps its spectra only when a backward pass can follow (grad mode on)
+    return SparseAzimuthPhase.apply(S, eps, w, o, method, torch.is_grad_enabled())
 
 
 def range_compress(raw, win=None, centred=True):

@@ -43,9 +43,14 @@ struct Layout {
 // H (digit-reversed order, carries 1/N) between conjugations, DIT, store.  FWD/DIT run the passes.
 // Row b of S/out uses row (b mod h_rows) of H (a stack of scans sharing one plan); conj_h applies conj(H), the
 // adjoint filter.
+// phase (optional): [n_rows / h_rows][N] per-column factors; row b is multiplied by phase row b / h_rows before
+// the filter (the scans of a stack each with its own phase correction).  spec (optional): [n_rows][N] the rows'
+// forward transforms (digit-reversed order, before the product with H), for the weight gradient.
 struct RowMap {
     int h_rows;
     int conj_h;
+    const float2 *phase;
+    float2 *spec;
 };
 
 template <typename FWD, typename INV>
@@ -68,8 +73,14 @@ __device__ __forceinline__ void row_filter(const float2 *__restrict__ S, const f
     for (int n = threadIdx.x; n < N; n += blockDim.x) cp_async8(x + rpad(n, pad_shift), S + row + n);
     cp_async_commit();
     cp_async_wait<0>();
+    if (map.phase) {                         // each thread scales the elements it staged
+        const float2 *ph = map.phase + (size_t)(blockIdx.x / map.h_rows) * N;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) x[rpad(n, pad_shift)] = cmul(x[rpad(n, pad_shift)], __ldg(ph + n));
+    }
     __syncthreads();
     fwd(x, tc, tf);
+    if (map.spec)
+        for (int n = threadIdx.x; n < N; n += blockDim.x) map.spec[row + n] = x[rpad(n, pad_shift)];
     if (lay.stage_h) {
         for (int n = threadIdx.x; n < N; n += blockDim.x) {   // spectrum times H (same digit-reversed order, carries 1/N), conjugated
             float2 h = hb[rpad(n, pad_shift)];
@@ -118,7 +129,9 @@ azimuth_fft_fixed_kernel(const float2 *__restrict__ S, const float2 *__restrict_
     extern __shared__ float2 sm[];
     const size_t row = (size_t)blockIdx.x * N;
     const size_t hrow = (size_t)(blockIdx.x % map.h_rows) * N;
-    filter_row_cta<T, N, stage_h_fits<N>(), R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm);
+    filter_row_cta<T, N, stage_h_fits<N>(), R...>(S + row, H + hrow, map.conj_h != 0, out + row, sm,
+                                                  map.phase ? map.phase + (size_t)(blockIdx.x / map.h_rows) * N : nullptr,
+                                                  map.spec ? map.spec + row : nullptr);
 }
 
 // dl != nullptr: plane blockIdx.y of the range-migration-aware plan, built from the taps of row r whose row
@@ -161,7 +174,8 @@ azimuth_plan_kernel(const float2 *__restrict__ w, const int32_t *__restrict__ o,
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
 azimuth_xspec_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St, const int32_t *__restrict__ o,
-                     int o_row_stride, int n_scans, int n_rng, int K, int N, RowPlan pl, float2 *__restrict__ grad_w) {
+                     int o_row_stride, int n_scans, int n_rng, int K, int N, RowPlan pl, float2 *__restrict__ grad_w,
+                     const float2 *__restrict__ phase) {
     extern __shared__ float2 sm[];
     const int pn = padded_len(N), sh = pl.pad_shift;
     float2 *P = sm;
@@ -180,6 +194,9 @@ azimuth_xspec_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St
         }
         cp_async_commit();
         cp_async_wait<0>();
+        if (phase)                            // S_t = S e^{j eps}: each thread scales the elements it staged
+            for (int n = threadIdx.x; n < N; n += blockDim.x)
+                y[rpad(n, sh)] = cmul(y[rpad(n, sh)], __ldg(phase + (size_t)sc * N + n));
         __syncthreads();
         row_dif(x, N, pl, tc, tf);
         row_dif(y, N, pl, tc, tf);
@@ -237,7 +254,8 @@ __device__ __forceinline__ void xspec_tail(float2 *x, float2 *y, float2 *P, cons
 template <int T, int N, int R1, int... Rs>
 __global__ void __launch_bounds__(T, 2)
 azimuth_xspec_fixed_kernel(const float2 *__restrict__ g, const float2 *__restrict__ St, const int32_t *__restrict__ o,
-                           int o_row_stride, int n_scans, int n_rng, int K, float2 *__restrict__ grad_w) {
+                           int o_row_stride, int n_scans, int n_rng, int K, float2 *__restrict__ grad_w,
+                           const float2 *__restrict__ phase) {
     extern __shared__ float2 sm[];
     cg::cluster_group cluster = cg::this_cluster();
     const int G = (int)cluster.num_blocks();
@@ -254,7 +272,7 @@ azimuth_xspec_fixed_kernel(const float2 *__restrict__ g, const float2 *__restric
     for (int sc = rank; sc < n_scans; sc += G) {
         const size_t row = ((size_t)sc * n_rng + r) * N;
         dif_first_global<N, R1, T, false>(g + row, x, tc, tf);
-        dif_first_global<N, R1, T, false>(St + row, y, tc, tf);
+        dif_first_global<N, R1, T, false>(St + row, y, tc, tf, false, phase ? phase + (size_t)sc * N : nullptr);
         xspec_tail<N, N / R1, T, Rs...>(x, y, P, tc, tf);
     }
     cluster.sync();
@@ -278,6 +296,75 @@ azimuth_xspec_fixed_kernel(const float2 *__restrict__ g, const float2 *__restric
         const int tau = pmod(__ldg(orow + k), N);
         grad_w[(size_t)r * K + k] = cscale(P[tau], inv_n);
     }
+}
+
+// Weight gradient from stored spectra (the forward filter's transforms X_s of the corrected rows and the adjoint
+// filter's transforms G_s of the image gradient, both digit-reversed), in two launches: the cross-spectrum
+// P[r][f] = sum_s G_s[r][f] conj(X_s[r][f]) elementwise (one thread per (row, frequency), scans in order: a pure
+// stream of 16 B per pixel), then per row one inverse-order DIT of P and the taps sampled.  No forward transform
+// is repeated.
+__global__ void __launch_bounds__(256)
+xspec_accumulate_kernel(const float2 *__restrict__ G, const float2 *__restrict__ X, int n_scans, long long plane,
+                        float2 *__restrict__ P) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= plane) return;
+    float2 p = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int sc = 0; sc < n_scans; ++sc) {
+        const float2 a = __ldg(G + sc * plane + i), b = __ldg(X + sc * plane + i);
+        p.x = fmaf(a.x, b.x, fmaf(a.y, b.y, p.x));     // P += G . conj(X)
+        p.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, p.y));
+    }
+    P[i] = p;
+}
+
+// rk > 0: the spectra came from the compile-time-plan filter, stored radix-major for its last radix rk (element
+// i = q*(N/rk) + b holds digit-reversed position b*rk + q); rk == 0: stored in digit-reversed order.
+template <typename INV>
+__device__ __forceinline__ void xspec_taps_row(const float2 *__restrict__ Pg, const int32_t *__restrict__ o,
+                                               int o_row_stride, int K, int N, int pad_shift, int rk,
+                                               float2 *__restrict__ grad_w, INV inv) {
+    extern __shared__ float2 sm[];
+    float2 *P = sm;
+    float2 *tw = P + padded_len(N);
+    const int r = blockIdx.x;
+    const float2 *tc, *tf;
+    build_twiddles(N, false, tw, &tc, &tf);
+    const int nb = rk > 0 ? N / rk : N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int q = i / nb, b = i - q * nb;
+        P[rpad(rk > 0 ? b * rk + q : i, pad_shift)] = __ldg(Pg + (size_t)r * N + i);
+    }
+    __syncthreads();
+    inv(P, tc, tf);
+    const float inv_n = (float)(1.0 / (double)N);
+    const int32_t *orow = o + (size_t)r * o_row_stride;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int tau = pmod(__ldg(orow + k), N);
+        grad_w[(size_t)r * K + k] = cscale(P[rpad(tau, pad_shift)], inv_n);
+    }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+xspec_taps_kernel(const float2 *__restrict__ P, const int32_t *__restrict__ o, int o_row_stride, int K, int N,
+                  RowPlan pl, float2 *__restrict__ grad_w) {
+    xspec_taps_row(P, o, o_row_stride, K, N, pl.pad_shift, 0, grad_w,
+                   [&](float2 *x, const float2 *tc, const float2 *tf) { row_dit(x, N, pl, tc, tf); });
+}
+
+template <int... R>
+constexpr int last_of() {
+    constexpr int r[] = {R...};
+    return r[sizeof...(R) - 1];
+}
+
+template <int T, int N, int... R>
+__global__ void __launch_bounds__(T, 2)
+xspec_taps_fixed_kernel(const float2 *__restrict__ P, const int32_t *__restrict__ o, int o_row_stride, int K,
+                        float2 *__restrict__ grad_w) {
+    xspec_taps_row(P, o, o_row_stride, K, N, 31, last_of<R...>(), grad_w,
+                   [](float2 *x, const float2 *tc, const float2 *tf) { dit_seq<N, N, false, T, R...>(x, tc, tf); });
 }
 
 constexpr size_t AF_SMEM_CAP = 200 * 1024;
@@ -365,8 +452,8 @@ bool try_fixed(int n_az, const RowPlan &pl, int n_rng, RowMap map, bool ov, cons
 }  // namespace
 
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
-                                bool overlap_predecessor, int h_rows, bool conj_h) {
-    const RowMap map{h_rows > 0 ? h_rows : n_rng, conj_h ? 1 : 0};
+                                bool overlap_predecessor, int h_rows, bool conj_h, const float2 *phase, float2 *spec) {
+    const RowMap map{h_rows > 0 ? h_rows : n_rng, conj_h ? 1 : 0, phase, spec};
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "azimuth_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
@@ -408,7 +495,7 @@ namespace {
 template <int T, int N, int... R>
 bool try_xspec_fixed(int n_az, const RowPlan &pl, const float2 *g, const float2 *S_t, const int32_t *o,
                      int o_row_stride, int n_scans, int n_rng, int K, float2 *grad_w, cudaStream_t s,
-                     rosar_status *st) {
+                     rosar_status *st, const float2 *phase) {
     constexpr int rad[] = {R...};
     if (n_az != N || threads_for(N) != T || pl.npass != (int)sizeof...(R) || n_rng > 65535) return false;
     for (int i = 0; i < pl.npass; ++i)
@@ -434,7 +521,7 @@ bool try_xspec_fixed(int n_az, const RowPlan &pl, const float2 *g, const float2 
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, azimuth_xspec_fixed_kernel<T, N, R...>, g, S_t, o, o_row_stride,
-                                             n_scans, n_rng, K, grad_w);
+                                             n_scans, n_rng, K, grad_w, phase);
     *st = e != cudaSuccess ? set_error(ROSAR_ERR_CUDA, "weight_grad_fft: launch failed: %s", cudaGetErrorString(e))
                            : check_launch("weight_grad_fft");
     return true;
@@ -443,17 +530,19 @@ bool try_xspec_fixed(int n_az, const RowPlan &pl, const float2 *g, const float2 
 }  // namespace
 
 rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
-                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s) {
+                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s,
+                                            const float2 *phase) {
     RowPlan pl;
     if (!make_plan(n_az, &pl))
         return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az, AF_MAX_N);
     {
         rosar_status st = ROSAR_OK;
         if (try_xspec_fixed<256, 3600, 16, 15, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s,
-                                                   &st) ||
+                                                   &st, phase) ||
             try_xspec_fixed<256, 1800, 8, 15, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s,
-                                                  &st) ||
-            try_xspec_fixed<256, 360, 8, 3, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s, &st))
+                                                  &st, phase) ||
+            try_xspec_fixed<256, 360, 8, 3, 15>(n_az, pl, g, S_t, o, o_row_stride, n_scans, n_rng, K, grad_w, s, &st,
+                                                phase))
             return st;
     }
     const size_t bytes = sizeof(float2) * (3 * (size_t)padded_len(n_az) + 64 + coarse_len(n_az));
@@ -464,11 +553,58 @@ rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, 
                                       (const void *)azimuth_xspec_kernel<512>, (const void *)azimuth_xspec_kernel<1024>};
     return launch_rows(
         n_az, n_rng, bytes,
-        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<256><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
-        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<384><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
-        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<512><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
-        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<1024><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<256><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w, phase); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<384><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w, phase); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<512><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w, phase); },
+        [&](int gr, int t, size_t sm) { azimuth_xspec_kernel<1024><<<gr, t, sm, s>>>(g, S_t, o, o_row_stride, n_scans, n_rng, K, n_az, pl, grad_w, phase); },
         ks, done, "weight_grad_fft");
+}
+
+namespace {
+template <int T, int N, int... R>
+bool try_xspec_taps_fixed(int n_az, const RowPlan &pl, const float2 *P, const int32_t *o, int o_row_stride, int n_rng,
+                          int K, float2 *grad_w, cudaStream_t s, rosar_status *st) {
+    constexpr int rad[] = {R...};
+    if (n_az != N || threads_for(N) != T || pl.pad_shift != 31 || pl.npass != (int)sizeof...(R)) return false;
+    for (int i = 0; i < pl.npass; ++i)
+        if (pl.rad[i] != rad[i]) return false;
+    static int done[kMaxDevices] = {};
+    const size_t smem = sizeof(float2) * ((size_t)padded_len(N) + 64 + coarse_len(N));
+    *st = ensure_smem((const void *)xspec_taps_fixed_kernel<T, N, R...>, smem, done, "weight_grad_spectra");
+    if (*st != ROSAR_OK) return true;
+    xspec_taps_fixed_kernel<T, N, R...><<<n_rng, T, smem, s>>>(P, o, o_row_stride, K, grad_w);
+    *st = check_launch("weight_grad_spectra");
+    return true;
+}
+}  // namespace
+
+rosar_status launch_azimuth_weight_grad_spectra(const float2 *G, const float2 *X, const int32_t *o, int o_row_stride,
+                                                int n_scans, int n_rng, int n_az, int K, float2 *P, float2 *grad_w,
+                                                cudaStream_t s) {
+    RowPlan pl;
+    if (!make_plan(n_az, &pl))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_spectra: n_az=%d is not 2^a 3^b 5^c in [2, %d]", n_az,
+                         AF_MAX_N);
+    const long long plane = (long long)n_rng * n_az;
+    xspec_accumulate_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, s>>>(G, X, n_scans, plane, P);
+    rosar_status st = check_launch("weight_grad_spectra");
+    if (st != ROSAR_OK) return st;
+    if (try_xspec_taps_fixed<256, 3600, 16, 15, 15>(n_az, pl, P, o, o_row_stride, n_rng, K, grad_w, s, &st) ||
+        try_xspec_taps_fixed<256, 1800, 8, 15, 15>(n_az, pl, P, o, o_row_stride, n_rng, K, grad_w, s, &st) ||
+        try_xspec_taps_fixed<512, 7200, 8, 4, 15, 15>(n_az, pl, P, o, o_row_stride, n_rng, K, grad_w, s, &st) ||
+        try_xspec_taps_fixed<256, 360, 8, 3, 15>(n_az, pl, P, o, o_row_stride, n_rng, K, grad_w, s, &st))
+        return st;
+    const size_t bytes = sizeof(float2) * ((size_t)padded_len(n_az) + 64 + coarse_len(n_az));
+    static int done[4][kMaxDevices] = {};
+    static const void *const ks[4] = {(const void *)xspec_taps_kernel<256>, (const void *)xspec_taps_kernel<384>,
+                                      (const void *)xspec_taps_kernel<512>, (const void *)xspec_taps_kernel<1024>};
+    return launch_rows(
+        n_az, n_rng, bytes,
+        [&](int gr, int t, size_t sm) { xspec_taps_kernel<256><<<gr, t, sm, s>>>(P, o, o_row_stride, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { xspec_taps_kernel<384><<<gr, t, sm, s>>>(P, o, o_row_stride, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { xspec_taps_kernel<512><<<gr, t, sm, s>>>(P, o, o_row_stride, K, n_az, pl, grad_w); },
+        [&](int gr, int t, size_t sm) { xspec_taps_kernel<1024><<<gr, t, sm, s>>>(P, o, o_row_stride, K, n_az, pl, grad_w); },
+        ks, done, "weight_grad_spectra");
 }
 
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,

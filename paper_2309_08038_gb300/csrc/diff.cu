@@ -35,29 +35,74 @@ phase_apply_kernel(const float2 *__restrict__ S, const float *__restrict__ eps, 
     for (int r = 0; r < n_rng; ++r) S_t[base + (size_t)r * n_az] = cmul(__ldg(S + base + (size_t)r * n_az), e);
 }
 
+// Phase gradients: CTA = 32 consecutive pulses x 8 row groups (256 threads).  Lane c of warp g owns pulse
+// n0 + c and rows g, g + 8, ...; the 8 group sums of a pulse are then added in group order, so every pulse's
+// sum runs in one fixed order (rows g mod 8 ascending within a group, groups 0..7).
+constexpr int PG_COLS = 32, PG_GROUPS = DG_THREADS / PG_COLS;
+
+// grad_eps[s][n] = sum_r Im(conj(a) b), a = S_t (or S * P), b = G; grad_S = G * conj(e) with e the phase factor.
+template <bool PHASOR>
+__device__ __forceinline__ void phase_grad_cta(const float2 *__restrict__ S, const float2 *__restrict__ P,
+                                               const float *__restrict__ eps, const float2 *__restrict__ G, int n_rng,
+                                               int n_az, float *__restrict__ grad_eps, float2 *__restrict__ grad_S) {
+    __shared__ float red[PG_GROUPS][PG_COLS];
+    const int c = threadIdx.x % PG_COLS, g = threadIdx.x / PG_COLS;
+    const int n = blockIdx.x * PG_COLS + c;
+    const int s = blockIdx.y;
+    float acc = 0.f;
+    if (n < n_az) {
+        const size_t base = (size_t)s * n_rng * n_az + n;
+        float2 e = make_float2(1.f, 0.f);                        // the forward's factor exp(j eps)
+        if (PHASOR) {
+            e = __ldg(P + (size_t)s * n_az + n);
+        } else if (grad_S) {
+            float sn, cs;
+            sincosf(__ldg(eps + (size_t)s * n_az + n), &sn, &cs);
+            e = make_float2(cs, sn);
+        }
+        const float2 ec = make_float2(e.x, -e.y);
+#pragma unroll 4
+        for (int r = g; r < n_rng; r += PG_GROUPS) {
+            const float2 sv = __ldg(S + base + (size_t)r * n_az);
+            const float2 a = PHASOR ? cmul(sv, e) : sv;
+            const float2 b = __ldg(G + base + (size_t)r * n_az);
+            acc = fmaf(a.x, b.y, acc);          // Im(conj(a) * b) = a.x*b.y - a.y*b.x
+            acc = fmaf(-a.y, b.x, acc);
+            if (grad_S) grad_S[base + (size_t)r * n_az] = cmul(b, ec);
+        }
+    }
+    red[g][c] = acc;
+    __syncthreads();
+    if (g == 0 && n < n_az && grad_eps) {
+        float t = red[0][c];
+#pragma unroll
+        for (int q = 1; q < PG_GROUPS; ++q) t += red[q][c];
+        grad_eps[(size_t)s * n_az + n] = t;
+    }
+}
+
 __global__ void __launch_bounds__(DG_THREADS)
 phase_grad_kernel(const float2 *__restrict__ S_t, const float2 *__restrict__ G, const float *__restrict__ eps,
                   int n_rng, int n_az, float *__restrict__ grad_eps, float2 *__restrict__ grad_S) {
-    const int n = blockIdx.x * DG_THREADS + threadIdx.x;
-    const int s = blockIdx.y;
-    if (n >= n_az) return;
-    const size_t base = (size_t)s * n_rng * n_az + n;
-    float2 e = make_float2(1.f, 0.f);
-    if (grad_S) {
-        float sn, cs;
-        sincosf(__ldg(eps + (size_t)s * n_az + n), &sn, &cs);
-        e = make_float2(cs, -sn);
-    }
-    float acc = 0.f;
-#pragma unroll 4
-    for (int r = 0; r < n_rng; ++r) {
-        const float2 a = __ldg(S_t + base + (size_t)r * n_az);
-        const float2 b = __ldg(G + base + (size_t)r * n_az);
-        acc = fmaf(a.x, b.y, acc);          // Im(conj(a) * b) = a.x*b.y - a.y*b.x
-        acc = fmaf(-a.y, b.x, acc);
-        if (grad_S) grad_S[base + (size_t)r * n_az] = cmul(b, e);
-    }
-    if (grad_eps) grad_eps[(size_t)s * n_az + n] = acc;
+    phase_grad_cta<false>(S_t, nullptr, eps, G, n_rng, n_az, grad_eps, grad_S);
+}
+
+// The phase factors e^{j eps} of every (scan, pulse) once, with the same sincosf as phase_apply_kernel.
+__global__ void __launch_bounds__(DG_THREADS)
+phasor_kernel(const float *__restrict__ eps, long long n, float2 *__restrict__ P) {
+    const long long i = (long long)blockIdx.x * DG_THREADS + threadIdx.x;
+    if (i >= n) return;
+    float sn, cs;
+    sincosf(__ldg(eps + i), &sn, &cs);
+    P[i] = make_float2(cs, sn);
+}
+
+// phase_grad_kernel with the corrected rows formed at load: S_t = S * P, grad_S = G * conj(P) (the same products
+// phase_apply_kernel and phase_grad_kernel compute, in the same order, so the results are identical).
+__global__ void __launch_bounds__(DG_THREADS)
+phase_grad_phasor_kernel(const float2 *__restrict__ S, const float2 *__restrict__ P, const float2 *__restrict__ G,
+                         int n_rng, int n_az, float *__restrict__ grad_eps, float2 *__restrict__ grad_S) {
+    phase_grad_cta<true>(S, P, nullptr, G, n_rng, n_az, grad_eps, grad_S);
 }
 
 // grad_w: one CTA of 1024 threads per range row.  Its 32 warps form TAPG tap groups x THG azimuth
@@ -192,9 +237,24 @@ rosar_status launch_phase_apply(const float2 *S, const float *eps, int n_scans, 
 rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *eps, int n_scans, int n_rng, int n_az,
                                float *grad_eps, float2 *grad_S, cudaStream_t s) {
     if (n_scans > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "phase_grad: n_scans=%d exceeds 65535", n_scans);
-    dim3 grid((n_az + DG_THREADS - 1) / DG_THREADS, n_scans);
+    dim3 grid((n_az + PG_COLS - 1) / PG_COLS, n_scans);
     phase_grad_kernel<<<grid, DG_THREADS, 0, s>>>(S_t, G, eps, n_rng, n_az, grad_eps, grad_S);
     return check_launch("phase_grad");
+}
+
+rosar_status launch_phase_grad_phasor(const float2 *S, const float2 *P, const float2 *G, int n_scans, int n_rng,
+                                      int n_az, float *grad_eps, float2 *grad_S, cudaStream_t s) {
+    if (n_scans > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "phase_grad_phasor: n_scans=%d exceeds 65535", n_scans);
+    dim3 grid((n_az + PG_COLS - 1) / PG_COLS, n_scans);
+    phase_grad_phasor_kernel<<<grid, DG_THREADS, 0, s>>>(S, P, G, n_rng, n_az, grad_eps, grad_S);
+    return check_launch("phase_grad_phasor");
+}
+
+rosar_status launch_phasors(const float *eps, long long n, float2 *P, cudaStream_t s) {
+    const long long blocks = (n + DG_THREADS - 1) / DG_THREADS;
+    if (blocks > 0x7fffffffLL) return set_error(ROSAR_ERR_UNSUPPORTED, "phasors: n=%lld too large", n);
+    phasor_kernel<<<(unsigned)blocks, DG_THREADS, 0, s>>>(eps, n, P);
+    return check_launch("phasors");
 }
 
 rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,

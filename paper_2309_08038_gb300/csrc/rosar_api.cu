@@ -576,6 +576,111 @@ rosar_status rosar_phase_grad(const rosar_c32 *S_t, const rosar_c32 *grad_S_t, c
                              static_cast<cudaStream_t>(stream));
 }
 
+rosar_status rosar_phasors(const float *eps, long long n, rosar_c32 *P, void *stream) {
+    clear_error();
+    if (!eps || !P) return set_error(ROSAR_ERR_INVALID_ARG, "phasors: null pointer argument");
+    if (n < 1) return set_error(ROSAR_ERR_INVALID_ARG, "phasors: n=%lld < 1", n);
+    if (misaligned(eps, 4) || misaligned(P, 8)) return set_error(ROSAR_ERR_INVALID_ARG, "phasors: misaligned pointer");
+    if (overlaps(P, sizeof(rosar_c32) * (size_t)n, eps, sizeof(float) * (size_t)n))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phasors: P overlaps eps");
+    return launch_phasors(eps, n, reinterpret_cast<float2 *>(P), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sparse_azimuth_fft_scans_ex(const rosar_c32 *S, const rosar_c32 *P, const rosar_c32 *H, int n_scans,
+                                              int n_rng, int n_az, int adjoint, rosar_c32 *out, rosar_c32 *spectrum,
+                                              void *stream) {
+    clear_error();
+    rosar_status st = check_stack("sparse_azimuth_fft_scans_ex", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!S || !H || !out) return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans_ex: null pointer argument");
+    if (adjoint != 0 && adjoint != 1)
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans_ex: adjoint must be 0 or 1");
+    if (misaligned(S, 8) || misaligned(H, 8) || misaligned(out, 8) || (P && misaligned(P, 8)) ||
+        (spectrum && misaligned(spectrum, 8)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans_ex: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az;
+    const size_t hb = sizeof(rosar_c32) * (size_t)n_rng * n_az, pb = sizeof(rosar_c32) * (size_t)n_scans * n_az;
+    if (overlaps(out, b, S, b) || overlaps(out, b, H, hb) || (P && overlaps(out, b, P, pb)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans_ex: out overlaps an input");
+    if (spectrum && (overlaps(spectrum, b, S, b) || overlaps(spectrum, b, H, hb) || overlaps(spectrum, b, out, b) ||
+                     (P && overlaps(spectrum, b, P, pb))))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sparse_azimuth_fft_scans_ex: spectrum overlaps another argument");
+    if (!azimuth_fft_supported(n_az))
+        return set_error(ROSAR_ERR_UNSUPPORTED, "sparse_azimuth_fft_scans_ex: n_az=%d is not 2^a 3^b 5^c <= 16384", n_az);
+    return launch_azimuth_fft(reinterpret_cast<const float2 *>(S), reinterpret_cast<const float2 *>(H), n_scans * n_rng,
+                              n_az, reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream), false, n_rng,
+                              adjoint == 1, reinterpret_cast<const float2 *>(P), reinterpret_cast<float2 *>(spectrum));
+}
+
+rosar_status rosar_azimuth_weight_grad_spectra(const rosar_c32 *G, const rosar_c32 *X, const int32_t *o,
+                                               int o_row_stride, int n_scans, int n_rng, int n_az, int K,
+                                               rosar_c32 *workspace, rosar_c32 *grad_w, void *stream) {
+    clear_error();
+    rosar_status st = check_stack("weight_grad_spectra", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!G || !X || !o || !workspace || !grad_w)
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: null pointer argument");
+    if (misaligned(workspace, 8)) return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: misaligned workspace");
+    {
+        const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az, wb = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+        if (overlaps(workspace, wb, G, b) || overlaps(workspace, wb, X, b) ||
+            overlaps(workspace, wb, grad_w, sizeof(rosar_c32) * (size_t)n_rng * K))
+            return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: workspace overlaps another argument");
+    }
+    if (K < 1 || (o_row_stride != 0 && o_row_stride < K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: K=%d o_row_stride=%d", K, o_row_stride);
+    if ((long long)n_rng * K > kMaxElems || (long long)n_rng * o_row_stride > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_spectra: sizes too large");
+    if (misaligned(G, 8) || misaligned(X, 8) || misaligned(o, 4) || misaligned(grad_w, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az, gw = sizeof(rosar_c32) * (size_t)n_rng * K;
+    if (overlaps(grad_w, gw, G, b) || overlaps(grad_w, gw, X, b))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_spectra: grad_w overlaps an input");
+    return launch_azimuth_weight_grad_spectra(reinterpret_cast<const float2 *>(G), reinterpret_cast<const float2 *>(X), o,
+                                              o_row_stride, n_scans, n_rng, n_az, K,
+                                              reinterpret_cast<float2 *>(workspace), reinterpret_cast<float2 *>(grad_w),
+                                              static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_azimuth_weight_grad_fft_phase(const rosar_c32 *g, const rosar_c32 *S, const rosar_c32 *P,
+                                                 const int32_t *o, int o_row_stride, int n_scans, int n_rng, int n_az,
+                                                 int K, rosar_c32 *grad_w, void *stream) {
+    clear_error();
+    if (!P) return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: null P");
+    if (misaligned(P, 8)) return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: misaligned P");
+    rosar_status st = check_stack("weight_grad_fft_phase", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (!g || !S || !o || !grad_w) return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: null pointer argument");
+    if (K < 1 || (o_row_stride != 0 && o_row_stride < K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: K=%d o_row_stride=%d", K, o_row_stride);
+    if ((long long)n_rng * K > kMaxElems || (long long)n_rng * o_row_stride > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "weight_grad_fft_phase: sizes too large");
+    if (misaligned(g, 8) || misaligned(S, 8) || misaligned(o, 4) || misaligned(grad_w, 8))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: misaligned pointer");
+    const size_t b = sizeof(rosar_c32) * (size_t)n_scans * n_rng * n_az, gw = sizeof(rosar_c32) * (size_t)n_rng * K;
+    if (overlaps(grad_w, gw, g, b) || overlaps(grad_w, gw, S, b) ||
+        overlaps(grad_w, gw, P, sizeof(rosar_c32) * (size_t)n_scans * n_az))
+        return set_error(ROSAR_ERR_INVALID_ARG, "weight_grad_fft_phase: grad_w overlaps an input");
+    return launch_azimuth_weight_grad_fft(reinterpret_cast<const float2 *>(g), reinterpret_cast<const float2 *>(S), o,
+                                          o_row_stride, n_scans, n_rng, n_az, K, reinterpret_cast<float2 *>(grad_w),
+                                          static_cast<cudaStream_t>(stream), reinterpret_cast<const float2 *>(P));
+}
+
+rosar_status rosar_phase_grad_phasor(const rosar_c32 *S, const rosar_c32 *P, const rosar_c32 *grad_S_t, int n_scans,
+                                     int n_rng, int n_az, float *grad_eps, rosar_c32 *grad_S, void *stream) {
+    clear_error();
+    if (!S || !P || !grad_S_t || (!grad_eps && !grad_S))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phase_grad_phasor: null pointer argument");
+    rosar_status st = check_stack("phase_grad_phasor", n_scans, n_rng, n_az);
+    if (st != ROSAR_OK) return st;
+    if (misaligned(S, 8) || misaligned(P, 8) || misaligned(grad_S_t, 8) || (grad_eps && misaligned(grad_eps, 4)) ||
+        (grad_S && misaligned(grad_S, 8)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "phase_grad_phasor: misaligned pointer");
+    return launch_phase_grad_phasor(reinterpret_cast<const float2 *>(S), reinterpret_cast<const float2 *>(P),
+                                    reinterpret_cast<const float2 *>(grad_S_t), n_scans, n_rng, n_az, grad_eps,
+                                    reinterpret_cast<float2 *>(grad_S), static_cast<cudaStream_t>(stream));
+}
+
 size_t rosar_image_l2_loss_workspace_bytes(void) { return sizeof(double) * (size_t)image_loss_partials(); }
 
 rosar_status rosar_image_l2_loss(const rosar_c32 *out, const rosar_c32 *ref, long long n, void *workspace,

@@ -86,6 +86,10 @@ rosar_status launch_azimuth_weight_grad(const float2 *g, const float2 *S_t, cons
                                         int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s);
 rosar_status launch_phase_grad(const float2 *S_t, const float2 *G, const float *eps, int n_scans, int n_rng, int n_az,
                                float *grad_eps, float2 *grad_S, cudaStream_t s);
+// The same with S uncorrected and the phase factors P = e^{j eps} [n_scans][n_az] given: S_t = S P is formed at load.
+rosar_status launch_phase_grad_phasor(const float2 *S, const float2 *P, const float2 *G, int n_scans, int n_rng,
+                                      int n_az, float *grad_eps, float2 *grad_S, cudaStream_t s);
+rosar_status launch_phasors(const float *eps, long long n, float2 *P, cudaStream_t s);
 rosar_status launch_range_compress_adjoint(const float2 *g, const float *win, int n_az, int L, int centred,
                                            float2 *grad_raw, cudaStream_t s, int n_scans = 1);
 
@@ -107,11 +111,21 @@ rosar_status launch_image_pipeline(const float2 *raw, const float *win, const fl
 // the stream writes S and nothing else the kernel reads before its grid-dependency wait, i.e. H).
 // h_rows: row b of S uses row (b mod h_rows) of H (0 = n_rng: one plan row per S row); conj_h: filter with conj(H),
 // the adjoint of the filter.
+// phase (optional): [n_rng / h_rows][n_az] factors applied to the rows of S as they are loaded; spec (optional):
+// [n_rng][n_az] receives the rows' forward transforms (digit-reversed, before the product with H).
 rosar_status launch_azimuth_fft(const float2 *S, const float2 *H, int n_rng, int n_az, float2 *out, cudaStream_t s,
-                                bool overlap_predecessor = false, int h_rows = 0, bool conj_h = false);
+                                bool overlap_predecessor = false, int h_rows = 0, bool conj_h = false,
+                                const float2 *phase = nullptr, float2 *spec = nullptr);
+// grad_w from the rows' stored transforms G (image gradient) and X (corrected S), [n_scans][n_rng][n_az] each;
+// P [n_rng][n_az] scratch for the cross-spectrum.
+rosar_status launch_azimuth_weight_grad_spectra(const float2 *G, const float2 *X, const int32_t *o, int o_row_stride,
+                                                int n_scans, int n_rng, int n_az, int K, float2 *P, float2 *grad_w,
+                                                cudaStream_t s);
 // grad_w[r][k] = sum_s sum_t g[s][r][t] conj(S_t[s][r][(t + o_k) mod n_az]) from the per-row cross-spectrum.
+// phase (optional): S_t = S_t[s] * phase[s] per column (the phase-corrected rows computed at load).
 rosar_status launch_azimuth_weight_grad_fft(const float2 *g, const float2 *S_t, const int32_t *o, int o_row_stride,
-                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s);
+                                            int n_scans, int n_rng, int n_az, int K, float2 *grad_w, cudaStream_t s,
+                                            const float2 *phase = nullptr);
 // dl != nullptr: the n_d planes of the range-migration-aware plan, plane i from the taps with dl = d_lo + i,
 // H [n_d][n_rng][n_az].
 rosar_status launch_azimuth_plan(const float2 *w, const int32_t *o, int o_row_stride, int n_rng, int n_az, int K,

@@ -300,15 +300,22 @@ __device__ __forceinline__ void dit_seq(float2 *x, const float2 *tc, const float
 // the closing barrier, so they are visible to the whole CTA after it.  discard: src is scratch that nothing
 // reads again, so after the barrier (every element has been read) the 128-byte L2 lines lying wholly inside
 // the row are dropped without being written back to memory; the lines it shares with neighbouring rows stay.
+// phase (optional, [N]): element n is multiplied by phase[n] as it is loaded (the per-pulse phase correction
+// of the differentiable form, S e^{j eps_n}, without a corrected copy of S in memory).
 template <int N, int R, int T, bool WAIT_ASYNC>
 __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src, float2 *x, const float2 *tc,
-                                                 const float2 *tf, bool discard = false) {
+                                                 const float2 *tf, bool discard = false,
+                                                 const float2 *__restrict__ phase = nullptr) {
     constexpr int s = N / R;
 #pragma unroll 1
     for (int j = threadIdx.x; j < s; j += T) {
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = __ldcg(src + j + r * s);
+        if (phase) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = cmul(v[r], __ldg(phase + j + r * s));
+        }
         small_dft<R>(v);
         x[j] = v[0];
         float2 wq[R];
@@ -329,8 +336,11 @@ __device__ __forceinline__ void dif_first_global(const float2 *__restrict__ src,
 // Last forward pass (blocks of R, stride 1), y = conj(H . X) (conj(H) . X conjugated when hs = -1), and the
 // first pass of the inverse on the same block.  H is in the forward transform's digit-reversed order; h is
 // shared memory (H_SMEM) or global.
+// spec (optional): the row's forward transform (before the product with H) is also written there, radix-major:
+// element r of block b (digit-reversed position b*R + r) at spec[r*(N/R) + b], so that a warp's stores of one r
+// are consecutive.
 template <int N, int R, int T, bool H_SMEM>
-__device__ __forceinline__ void fused_mid(float2 *x, const float2 *h, float hs) {
+__device__ __forceinline__ void fused_mid(float2 *x, const float2 *h, float hs, float2 *__restrict__ spec = nullptr) {
     constexpr int nb = N / R;
 #pragma unroll 1
     for (int b = threadIdx.x; b < nb; b += T) {
@@ -339,6 +349,10 @@ __device__ __forceinline__ void fused_mid(float2 *x, const float2 *h, float hs) 
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = x[base + r];
         small_dft<R>(v);
+        if (spec) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) spec[r * nb + b] = v[r];
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             float2 hv = H_SMEM ? h[base + r] : __ldg(h + base + r);
@@ -372,13 +386,14 @@ __device__ __forceinline__ void dit_last_global(const float2 *x, float2 *__restr
 }
 
 template <int N, int M, int T, bool H_SMEM, int R, int... Rest>
-__device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float hs, const float2 *tc, const float2 *tf) {
+__device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float hs, const float2 *tc, const float2 *tf,
+                                              float2 *__restrict__ spec = nullptr) {
     if constexpr (sizeof...(Rest) == 0) {
         static_assert(M == R, "the last radix spans the last block");
-        fused_mid<N, R, T, H_SMEM>(x, h, hs);
+        fused_mid<N, R, T, H_SMEM>(x, h, hs, spec);
     } else {
         dif_pass_c<N, M, R, false, T>(x, tc, tf);
-        filter_middle<N, M / R, T, H_SMEM, Rest...>(x, h, hs, tc, tf);
+        filter_middle<N, M / R, T, H_SMEM, Rest...>(x, h, hs, tc, tf, spec);
         dit_pass_c<N, M, R, false, T>(x, tc, tf);
     }
 }
@@ -390,10 +405,11 @@ __device__ __forceinline__ void filter_middle(float2 *x, const float2 *h, float 
 template <int N, int T, bool H_SMEM, int R1, int... Rs>
 __device__ __forceinline__ void row_filter_fused(const float2 *__restrict__ src, const float2 *h, float hs, float2 *x,
                                                  float2 *__restrict__ dst, const float2 *tc, const float2 *tf,
-                                                 bool discard = false) {
+                                                 bool discard = false, const float2 *__restrict__ phase = nullptr,
+                                                 float2 *__restrict__ spec = nullptr) {
     static_assert(sizeof...(Rs) >= 1, "at least two passes");
-    dif_first_global<N, R1, T, H_SMEM>(src, x, tc, tf, discard);
-    filter_middle<N, N / R1, T, H_SMEM, Rs...>(x, h, hs, tc, tf);
+    dif_first_global<N, R1, T, H_SMEM>(src, x, tc, tf, discard, phase);
+    filter_middle<N, N / R1, T, H_SMEM, Rs...>(x, h, hs, tc, tf, spec);
     dit_last_global<N, R1, T>(x, dst, tc, tf);
 }
 
@@ -466,7 +482,9 @@ constexpr size_t filter_row_smem() {
 
 template <int T, int N, bool H_SMEM, int... R>
 __device__ __forceinline__ void filter_row_cta(const float2 *__restrict__ S_row, const float2 *__restrict__ H_row,
-                                               bool conj_h, float2 *__restrict__ out_row, float2 *sm) {
+                                               bool conj_h, float2 *__restrict__ out_row, float2 *sm,
+                                               const float2 *__restrict__ phase = nullptr,
+                                               float2 *__restrict__ spec = nullptr) {
     static_assert(pad_shift_for(N) == 31, "compile-time filter plans are for rows with an odd factor");
     float2 *x = sm;
     float2 *hb = x + padded_len(N);
@@ -479,7 +497,8 @@ __device__ __forceinline__ void filter_row_cta(const float2 *__restrict__ S_row,
     build_twiddles(N, false, tw, &tc, &tf);
     __syncthreads();
     griddep_wait();                          // S is complete (no-op unless launched to overlap its producer)
-    row_filter_fused<N, T, H_SMEM, R...>(S_row, H_SMEM ? hb : H_row, conj_h ? -1.f : 1.f, x, out_row, tc, tf);
+    row_filter_fused<N, T, H_SMEM, R...>(S_row, H_SMEM ? hb : H_row, conj_h ? -1.f : 1.f, x, out_row, tc, tf, false,
+                                         phase, spec);
 }
 
 inline int threads_for(int N) { return N <= 4096 ? 256 : N <= 8192 ? 512 : 1024; }

@@ -363,6 +363,82 @@ def azimuth_weight_grad_fft(g, S_t, o, K, out=None, stream=None):
     return out
 
 
+def phasors(eps, out=None, stream=None):
+    """rosar_phasors: P = exp(j*eps) elementwise (eps float32, any shape; P complex64 of the same shape)."""
+    lib = _lib.load()
+    require(eps, torch.float32, "eps", ndim=eps.dim())
+    if out is None:
+        out = torch.empty(eps.shape, dtype=torch.complex64, device=eps.device)
+    require(out, torch.complex64, "P", shape=tuple(eps.shape))
+    check(lib.rosar_phasors(ptr(eps), eps.numel(), ptr(out), stream_handle(stream)))
+    return out
+
+
+def sparse_azimuth_fft_scans_ex(S, H, P=None, adjoint=False, spectrum=None, out=None, stream=None):
+    """rosar_sparse_azimuth_fft_scans_ex: the frequency-domain filter (adjoint: with conj(H)) of S [n_scans, n_rng,
+    n_az], each scan's columns multiplied by P [n_scans, n_az] as they are loaded (P None: none); spectrum (a tensor
+    like S, or None) receives the rows' forward transforms."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    if P is not None:
+        require(P, torch.complex64, "P", shape=(n_scans, n_az))
+    require(H, torch.complex64, "H", shape=(n_rng, n_az))
+    if spectrum is not None:
+        require(spectrum, torch.complex64, "spectrum", shape=(n_scans, n_rng, n_az))
+    if out is None:
+        out = torch.empty_like(S)
+    require(out, torch.complex64, "out", shape=(n_scans, n_rng, n_az))
+    check(lib.rosar_sparse_azimuth_fft_scans_ex(ptr(S), ptr(P), ptr(H), n_scans, n_rng, n_az, int(bool(adjoint)),
+                                                ptr(out), ptr(spectrum), stream_handle(stream)))
+    return out
+
+
+def azimuth_weight_grad_spectra(G, X, o, K, workspace=None, out=None, stream=None):
+    """rosar_azimuth_weight_grad_spectra: grad_w [n_rng, K] from the adjoint call's spectrum G and the forward call's
+    spectrum X (both [n_scans, n_rng, n_az]); workspace [n_rng, n_az] holds the cross-spectrum."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(X, "X")
+    require(G, torch.complex64, "G", shape=(n_scans, n_rng, n_az))
+    stride = _offsets(o, n_rng, K)
+    if workspace is None:
+        workspace = torch.empty((n_rng, n_az), dtype=torch.complex64, device=X.device)
+    require(workspace, torch.complex64, "workspace", shape=(n_rng, n_az))
+    if out is None:
+        out = torch.empty((n_rng, K), dtype=torch.complex64, device=X.device)
+    require(out, torch.complex64, "grad_w", shape=(n_rng, K))
+    check(lib.rosar_azimuth_weight_grad_spectra(ptr(G), ptr(X), ptr(o), stride, n_scans, n_rng, n_az, K,
+                                                ptr(workspace), ptr(out), stream_handle(stream)))
+    return out
+
+
+def azimuth_weight_grad_fft_phase(g, S, P, o, K, out=None, stream=None):
+    """rosar_azimuth_weight_grad_fft_phase: rosar_azimuth_weight_grad_fft with S_t = S * P formed at load."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    require(g, torch.complex64, "g", shape=(n_scans, n_rng, n_az))
+    require(P, torch.complex64, "P", shape=(n_scans, n_az))
+    stride = _offsets(o, n_rng, K)
+    if out is None:
+        out = torch.empty((n_rng, K), dtype=torch.complex64, device=S.device)
+    require(out, torch.complex64, "grad_w", shape=(n_rng, K))
+    check(lib.rosar_azimuth_weight_grad_fft_phase(ptr(g), ptr(S), ptr(P), ptr(o), stride, n_scans, n_rng, n_az, K,
+                                                  ptr(out), stream_handle(stream)))
+    return out
+
+
+def phase_grad_phasor(S, P, grad_S_t, want_eps=True, want_S=False, stream=None):
+    """rosar_phase_grad_phasor: (grad_eps [n_scans, n_az] or None, grad_S or None) with S_t = S * P formed at load."""
+    lib = _lib.load()
+    n_scans, n_rng, n_az = _stack(S, "S")
+    require(P, torch.complex64, "P", shape=(n_scans, n_az))
+    require(grad_S_t, torch.complex64, "grad_S_t", shape=(n_scans, n_rng, n_az))
+    ge = torch.empty((n_scans, n_az), dtype=torch.float32, device=S.device) if want_eps else None
+    gS = torch.empty_like(S) if want_S else None
+    check(lib.rosar_phase_grad_phasor(ptr(S), ptr(P), ptr(grad_S_t), n_scans, n_rng, n_az, ptr(ge), ptr(gS),
+                                      stream_handle(stream)))
+    return ge, gS
+
+
 def phase_grad(S_t, grad_S_t, eps, want_eps=True, want_S=False, stream=None):
     """rosar_phase_grad: (grad_eps [n_scans, n_az] or None, grad_S or None)."""
     lib = _lib.load()

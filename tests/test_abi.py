@@ -214,3 +214,19 @@ def test_migrating_fft_rejects_bad_arguments(lib):
     assert b"1031" in lib.rosar_last_error()
     g = lib.rosar_image_migrating_fft
     assert g(FAKE, None, FAKE2, 0, 2, 3600, 48, FAKE3, FAKE4, None) == 2          # L not a power of two
+
+
+def test_fused_phase_calls_reject_bad_arguments(lib):
+    FAKE3 = ctypes.c_void_p(0x30000000)
+    assert lib.rosar_phasors(None, 10, FAKE2, None) == 1
+    assert lib.rosar_phasors(FAKE, 0, FAKE2, None) == 1
+    assert lib.rosar_phasors(FAKE, 10, FAKE, None) == 1                                   # P overlaps eps
+    f = lib.rosar_sparse_azimuth_fft_scans_ex
+    assert f(FAKE, None, None, 2, 4, 3600, 0, FAKE3, None, None) == 1                    # null H
+    assert f(FAKE, None, FAKE2, 2, 4, 3600, 2, FAKE3, None, None) == 1                   # adjoint not 0/1
+    assert f(FAKE, None, FAKE2, 2, 4, 3600, 0, FAKE3, FAKE3, None) == 1                  # spectrum aliases out
+    assert f(FAKE, FAKE2, FAKE3, 2, 4, 1031, 0, ctypes.c_void_p(0x40000000), None, None) == 2   # no FFT plan
+    assert lib.rosar_azimuth_weight_grad_spectra(FAKE, None, FAKE3, 0, 2, 4, 3600, 8, FAKE2, FAKE3, None) == 1
+    assert lib.rosar_azimuth_weight_grad_spectra(FAKE, FAKE2, FAKE3, 0, 2, 4, 3600, 8, FAKE, FAKE3, None) == 1  # ws = G
+    assert lib.rosar_azimuth_weight_grad_fft_phase(FAKE, FAKE2, None, FAKE3, 0, 2, 4, 3600, 8, FAKE3, None) == 1
+    assert lib.rosar_phase_grad_phasor(FAKE, FAKE2, FAKE3, 2, 4, 3600, None, None, None) == 1   # nothing to compute

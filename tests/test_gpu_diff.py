@@ -268,3 +268,77 @@ def test_frequency_domain_adjoints_match_oracle(rosar, n_az, per_row, n_scans):
         assert _rel(adj[s], O.sparse_azimuth_adjoint_S(g[s], w, o)) < 1e-5
         ref_w += O.sparse_azimuth_adjoint_w(g[s], S[s], o)
     assert _rel(gw, ref_w) < 1e-5
+
+
+@pytest.mark.parametrize("n_az,per_row,n_scans", [(3600, False, 16), (1800, True, 3), (1000, False, 2), (360, True, 5)])
+def test_phase_fused_kernels_equal_the_materialized_path(rosar, n_az, per_row, n_scans):
+    """The frequency-domain step without S_t in memory (phase factors applied as S is loaded) gives the same bits
+    as rosar_phase_apply followed by the filter, the weight gradient and the phase gradient on S_t; and matches the
+    oracle (compile-time plans 3600/1800/360 and the run-time plan of 1000 pulses)."""
+    import torch
+    rng = np.random.default_rng(n_az + 7)
+    n_rng, K = 5, 12
+    M = min(n_az, 600)
+    if per_row:
+        o = np.stack([np.sort(rng.choice(M, K, replace=False)) - M // 2 for _ in range(n_rng)]).astype(np.int32)
+    else:
+        o = (np.sort(rng.choice(M, K, replace=False)) - M // 2).astype(np.int32)
+    S, g, w = _c(rng, n_scans, n_rng, n_az), _c(rng, n_scans, n_rng, n_az), _c(rng, n_rng, K)
+    eps = (rng.standard_normal((n_scans, n_az)) * 0.3).astype(np.float32)
+    tS, tg, tw, to, te = (_cuda(torch, x) for x in (S, g, w, o, eps))
+    H = rosar.azimuth_plan(tw, to, n_az)
+    P = rosar.phasors(te)
+    S_t = rosar.phase_apply(tS, te)
+    X, G = torch.empty_like(tS), torch.empty_like(tS)
+    out = rosar.sparse_azimuth_fft_scans_ex(tS, H, P=P, spectrum=X)
+    assert torch.equal(out, rosar.sparse_azimuth_fft_scans(S_t, H))
+    adj = rosar.sparse_azimuth_fft_scans_ex(tg, H, adjoint=True, spectrum=G)
+    assert torch.equal(adj, rosar.sparse_azimuth_fft_scans(tg, H, adjoint=True))
+    assert torch.equal(rosar.azimuth_weight_grad_fft_phase(tg, tS, P, to, K), rosar.azimuth_weight_grad_fft(tg, S_t, to, K))
+    ge1, gs1 = rosar.phase_grad_phasor(tS, P, tg, want_eps=True, want_S=True)
+    ge0, gs0 = rosar.phase_grad(S_t, tg, te, want_eps=True, want_S=True)
+    assert torch.equal(ge1, ge0) and torch.equal(gs1, gs0)
+    out = out.cpu().numpy()
+    ref_w = np.zeros((n_rng, K), np.complex128)
+    for s in range(n_scans):
+        St = O.apply_phase_errors(S[s], eps[s])
+        assert _rel(out[s], O.sparse_azimuth(St, w, o)) < 1e-5
+        ref_w += O.sparse_azimuth_adjoint_w(g[s], St, o)
+    # the weight gradient from the two calls' stored spectra
+    assert _rel(rosar.azimuth_weight_grad_spectra(G, X, to, K).cpu().numpy(), ref_w) < 1e-5
+
+
+def test_differentiable_step_replays_from_a_cuda_graph(rosar):
+    """Forward, image loss and backward of the frequency-domain form captured in one CUDA graph: every replay
+    gives the eager step's loss and gradients bit for bit (the benchmark times the step this way too)."""
+    import torch
+    rng = np.random.default_rng(21)
+    n_scans, n_rng, n_az, K = 3, 16, 3600, 24
+    S = _cuda(torch, _c(rng, n_scans, n_rng, n_az))
+    B = _cuda(torch, _c(rng, n_scans, n_rng, n_az))
+    o = _cuda(torch, (np.sort(rng.choice(600, K, replace=False)) - 300).astype(np.int32))
+    w = _cuda(torch, _c(rng, n_rng, K)).requires_grad_(True)
+    eps = _cuda(torch, (rng.standard_normal((n_scans, n_az)) * 0.3).astype(np.float32)).requires_grad_(True)
+
+    def step():
+        loss = rosar.autograd.image_l2_loss(rosar.autograd.sparse_azimuth_phase(S, eps, w, o, method="fft"), B)
+        loss.backward()
+        return loss
+
+    ref_loss = step().detach().clone()
+    ref_w, ref_e = w.grad.clone(), eps.grad.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        w.grad = eps.grad = None
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    w.grad = eps.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        loss = step()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(loss, ref_loss)
+        assert torch.equal(w.grad, ref_w) and torch.equal(eps.grad, ref_e)
