@@ -19,6 +19,12 @@
 // depends on (r, d) only; that kernel variant tabulates (x, alpha*phase) per d
 // and the pixel loop is two gathers, an interpolation and a complex MAC.
 //
+// With supplied errors the fine phase exp(-j*2*pi*(2*f_mid/c)*delta) of every (pixel, pulse) is taken as
+// sin/cos of an angle first reduced exactly by whole turns to [-pi, pi] (delta spans tens of cycles) and then
+// evaluated by the hardware sine and cosine (about 1e-6 absolute error there), instead of the accurate
+// sincospif's software range reduction and polynomials: the per-sample work is issue-bound FP32 and SFU.
+// The interpolation mode is a template parameter.
+//
 // Grid: (azimuth tiles of 256 pixels, rows).  Compute-bound (FP32 + SFU) once S is staged in shared memory.
 
 #include "rosar_internal.cuh"
@@ -41,10 +47,19 @@ __device__ __forceinline__ float2 read_bin(const float2 *__restrict__ S, int l, 
 // (one bin of margin each side) and the pulses th0 + dc .. th0 + dc + BPA_WC are staged in shared memory once, and
 // every (pixel, pulse) sample whose two bins fall in the window reads it there (others, e.g. under large supplied
 // position errors, read S through L2 as before).
-template <bool NOMINAL>
+// exp(-j*pi*x) for |x| up to 2^22: x reduced by whole turns (x - 2*rint(x/2), exact) to [-1, 1], then the
+// hardware sine and cosine of pi times the remainder.
+__device__ __forceinline__ float2 expmjpi_fast(float x) {
+    const float xr = fmaf(-2.f, rintf(0.5f * x), x);
+    float sn, cs;
+    __sincosf(3.14159265358979f * xr, &sn, &cs);
+    return make_float2(cs, -sn);
+}
+
+template <bool NOMINAL, bool LINEAR>
 __global__ void __launch_bounds__(BPA_THREADS)
 bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ dphi, const float *__restrict__ dr,
-           int L, int n_az, int M_ap, int interp, float2 *__restrict__ out) {
+           int L, int n_az, int M_ap, float2 *__restrict__ out) {
     extern __shared__ float2 wsm[];                           // [BPA_WR][BPA_WC]
     __shared__ float4 dtab[BPA_DC];                           // NOMINAL: (x, a.re, a.im, -); else (sin, cos, x_nominal, -)
     __shared__ float4 ptab[NOMINAL ? 1 : BPA_THREADS + BPA_DC];   // per pulse (cos(eps/2), sin(eps/2), dr, -)
@@ -167,14 +182,13 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                         delta = 0.f;
                         alpha = 1.f;
                     }
-                    float ps, pc;
-                    sincospif(2.f * p.two_f_over_c * delta, &ps, &pc);
+                    const float2 ph = expmjpi_fast(2.f * p.two_f_over_c * delta);
                     x = fmaf(delta, p.inv_dR, rf);
-                    a = make_float2(alpha * pc, -alpha * ps);
+                    a = make_float2(alpha * ph.x, alpha * ph.y);
                 }
                 const int col = threadIdx.x + i;
                 float2 sv;
-                if (interp) {
+                if (LINEAR) {
                     const float fl = floorf(x);
                     const int l0 = (int)fl;
                     const float f = x - fl;
@@ -205,15 +219,19 @@ rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, 
                         int n_az, int M_ap, int interp, float2 *out, cudaStream_t s) {
     if (n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "bpa: n_rng=%d exceeds 65535", n_rng);
     dim3 grid((n_az + BPA_THREADS - 1) / BPA_THREADS, n_rng);
-    static int done[2][kMaxDevices] = {};
+    static int done[4][kMaxDevices] = {};
     const bool nominal = dphi == nullptr && dr == nullptr;
-    rosar_status st = nominal ? ensure_smem((const void *)bpa_kernel<true>, BPA_SMEM, done[0], "bpa")
-                              : ensure_smem((const void *)bpa_kernel<false>, BPA_SMEM, done[1], "bpa");
+    const int v = (nominal ? 0 : 2) + (interp ? 1 : 0);
+    static const void *const ks[4] = {(const void *)bpa_kernel<true, false>, (const void *)bpa_kernel<true, true>,
+                                      (const void *)bpa_kernel<false, false>, (const void *)bpa_kernel<false, true>};
+    rosar_status st = ensure_smem(ks[v], BPA_SMEM, done[v], "bpa");
     if (st != ROSAR_OK) return st;
-    if (nominal)
-        bpa_kernel<true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
-    else
-        bpa_kernel<false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, interp, out);
+    switch (v) {
+        case 0: bpa_kernel<true, false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        case 1: bpa_kernel<true, true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        case 2: bpa_kernel<false, false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        default: bpa_kernel<false, true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+    }
     return check_launch("bpa");
 }
 
