@@ -116,7 +116,10 @@ struct Tile {
     static constexpr int NF = L >= 16 ? LG / 4 : 0;    // full radix-16 passes
     static constexpr int RR = L >= 16 ? (L >> (4 * NF)) : 1;   // remainder radix (1 = none)
     static constexpr int LP = L + L / 16;              // padded per-pulse stride in the FFT buffer
-    static constexpr int TP = P + 2;                   // row stride of the transposed tile (16-B aligned)
+    // row stride of the transposed tile: the last pass's stores tile[l*TP + p] hit 16 distinct 8-byte bank pairs per
+    // half-warp (T threads per pulse: 16/T pulses of a half-warp differ by TP = 16/T mod 16; T >= 16: odd TP)
+    static constexpr int TP = P + (T >= 16 ? 1 : 16 / T);
+    static constexpr bool TP_EVEN = TP % 2 == 0;       // rows 16-byte aligned: pairs of pulses copied as float4
     static constexpr int BUF = (P * LP > L * TP) ? P * LP : L * TP;
     static constexpr int THREADS = T * P;
     static constexpr int TAB = 32 + ((2 * L + 31) / 32 + 1) / 2 * 2;   // two-level table, even (16-B alignment)
@@ -237,9 +240,16 @@ __device__ __forceinline__ void range_tile(const float2 *__restrict__ raw, const
     // coalesced store of the transposed tile: row l holds pulses n0..n0+P-1
     const int np = min(P, n_az - n0);
     if (vec_store && np == P) {
+        // pairs of pulses as one 16-byte store; rows of an odd stride are read as two 8-byte halves
         for (int idx = threadIdx.x; idx < L * (P / 2); idx += PL::THREADS) {
             const int l = idx / (P / 2), q = idx % (P / 2);
-            const float4 val = *reinterpret_cast<const float4 *>(buf + l * PL::TP + 2 * q);
+            float4 val;
+            if constexpr (PL::TP_EVEN) {
+                val = *reinterpret_cast<const float4 *>(buf + l * PL::TP + 2 * q);
+            } else {
+                const float2 a = buf[l * PL::TP + 2 * q], b = buf[l * PL::TP + 2 * q + 1];
+                val = make_float4(a.x, a.y, b.x, b.y);
+            }
             *reinterpret_cast<float4 *>(S + (size_t)l * n_az + n0 + 2 * q) = val;
         }
     } else {

@@ -210,10 +210,10 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     }
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[i])), "r"(PRODUCERS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[i])), "r"(PRODUCERS / 32));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&empty[i])), "r"(1));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(fold_bar)), "r"(PRODUCERS));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(fold_bar)), "r"(PRODUCERS / 32));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     auto tap_off = [&](int kk) -> int {
@@ -356,8 +356,15 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
                 for (int i = 0; i < 4; ++i) {
                     const float wm = win ? __ldg(win + mb + i) : 1.f;
                     const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
-                    split2(v.x, -v.y, re_hi[i], re_lo[i]);
-                    split2(v.y, v.x, im_hi[i], im_lo[i]);
+                    // one split of (v.re, v.im); rounding is symmetric and per component, so the row (re) =
+                    // (v.re, -v.im) is the same pairs with the high half's sign flipped and the row (im) =
+                    // (v.im, v.re) the same pairs with the halves swapped
+                    uint32_t hi, lo;
+                    split2(v.x, v.y, hi, lo);
+                    re_hi[i] = hi ^ 0x80000000u;
+                    re_lo[i] = lo ^ 0x80000000u;
+                    im_hi[i] = __byte_perm(hi, 0, 0x1032);
+                    im_lo[i] = __byte_perm(lo, 0, 0x1032);
                     e = cmul(e, step);
                 }
                 const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
@@ -369,14 +376,18 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
                 *reinterpret_cast<uint4 *>(st + 2 * TILE + b_second) = b_swap ? rh : ih;
                 *reinterpret_cast<uint4 *>(st + 3 * TILE + b_second) = b_swap ? rl : il;
             }
+            // every thread makes its tile stores visible to the tensor core's (async) proxy; the warp then arrives
+            // once (one arrival per warp: 256 arrivals on one word would serialise in shared memory)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[b])) : "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[b])) : "memory");
             if ((s + 1) % PERIOD == 0 && s + 1 < stages) {   // end of a period: its MMAs done, fold X into Y
                 if (ok) ok = wait_bar(&empty[b], (uint32_t)((s >> 1) & 1));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (ok) fold();
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(fold_bar)) : "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(fold_bar)) : "memory");
             }
         }
         if (ok && stages > 0) ok = wait_bar(&empty[(stages - 1) & 1], (uint32_t)(((stages - 1) >> 1) & 1));
