@@ -62,7 +62,10 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
            int L, int n_az, int M_ap, float2 *__restrict__ out) {
     extern __shared__ float2 wsm[];                           // [BPA_WR][BPA_WC]
     __shared__ float4 dtab[BPA_DC];                           // NOMINAL: (x, a.re, a.im, -); else (sin, cos, x_nominal, -)
-    __shared__ float4 ptab[NOMINAL ? 1 : BPA_THREADS + BPA_DC];   // per pulse (cos(eps/2), sin(eps/2), dr, -)
+    // per pulse, with this CTA's row folded in: (cos(eps/2), sin(eps/2), dr*(r_n + r0 - 2R), 4*R*r_n), and
+    // rho - dr (the numerator of cos(theta') before its sin^2 term)
+    __shared__ float4 ptab[NOMINAL ? 1 : BPA_THREADS + BPA_DC];
+    __shared__ float pal[NOMINAL ? 1 : BPA_THREADS + BPA_DC];
     __shared__ float2 rowph;
     __shared__ float red_lo[BPA_THREADS / 32], red_hi[BPA_THREADS / 32];
 
@@ -122,7 +125,10 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                 const float e = dphi ? __ldg(dphi + n) : 0.f;
                 float se, ce;
                 sincosf(0.5f * e, &se, &ce);
-                ptab[i] = make_float4(ce, se, dr ? __ldg(dr + n) : 0.f, 0.f);
+                const float drn = dr ? __ldg(dr + n) : 0.f;
+                const float rn = r0 + drn;
+                ptab[i] = make_float4(ce, se, drn * (rn + r0 - 2.f * R), 4.f * R * rn);
+                pal[i] = rho - drn;
             }
         }
         // window rows from the chunk's nominal x range
@@ -168,16 +174,14 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                     const float4 pp = ptab[threadIdx.x + i];
                     const float sh = fmaf(t.x, pp.x, t.y * pp.y);            // sin((pi*d/n_az) + eps/2)
                     const float s2 = sh * sh;
-                    const float drn = pp.z;
-                    const float rn = r0 + drn;
-                    const float num = fmaf(drn, rn + r0 - 2.f * R, 4.f * R * rn * s2);
+                    const float num = fmaf(pp.w, s2, pp.z);                  // R_n^2 - rho^2
                     const float Rn2 = fmaf(rho, rho, num);
                     float delta, alpha;
                     if (Rn2 > 0.f) {
                         const float inv = rsqrtf(Rn2);
                         const float Rn = Rn2 * inv;
                         delta = __fdividef(num, Rn + rho);
-                        alpha = fmaxf(0.f, fmaf(-2.f * R, s2, rho - drn) * inv);
+                        alpha = fmaxf(0.f, fmaf(-2.f * R, s2, pal[threadIdx.x + i]) * inv);
                     } else {
                         delta = 0.f;
                         alpha = 1.f;
@@ -200,7 +204,7 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                         s0 = read_bin(S, l0, L, n, n_az);
                         s1 = read_bin(S, l0 + 1, L, n, n_az);
                     }
-                    sv = make_float2(fmaf(f, s1.x - s0.x, s0.x), fmaf(f, s1.y - s0.y, s0.y));
+                    sv = caxpy(f, csub(s1, s0), s0);
                 } else {
                     const int l0 = (int)floorf(x + 0.5f);
                     sv = (l0 >= wlo && l0 < wtop) ? wsm[(l0 - wlo) * BPA_WC + col] : read_bin(S, l0, L, n, n_az);
