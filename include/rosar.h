@@ -229,6 +229,31 @@ ROSAR_API rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, co
                                       int o_row_stride, const rosar_radar *radar, int n_az, int L, int n_rng, int K,
                                       int centred, rosar_c32 *out, void *stream);
 
+/*
+ * The time-domain forms with their B operand precomputed once per weight design (a "plan"):
+ * B[tap][sample][row] = c * win[m] * exp(-j*pi*phi*(m - m_ref)), the coefficient, window and fast-time
+ * phasor of Eq. (14) / Algorithm 2's W_SA, split into bf16 hi and lo parts.  It depends on the radar
+ * geometry, the window and the weights, not on the raw cube, so a caller imaging many scans with one design
+ * computes it once; each planned call then only streams the raw cube through the tensor cores.  Same sums
+ * as rosar_bpa_time / rosar_sas_time (shared offsets), each sample's phasor taken directly instead of by
+ * recurrence (float32 rounding differs).
+ *   rosar_time_domain_plan_bytes: size of a plan, 8 * n_rng * L * K bytes (K = M_ap for BPA).
+ *   rosar_sas_time_plan / rosar_bpa_time_plan: write the plan (device, 16-byte aligned, >= the size above);
+ *     arguments as rosar_sas_time (shared offsets o [K]) / rosar_bpa_time.
+ *   rosar_sas_time_planned / rosar_bpa_time_planned: the image from raw [n_az][L] with the plan; o is the
+ *     plan's offsets [K].  Limits as the unplanned calls.
+ */
+ROSAR_API size_t rosar_time_domain_plan_bytes(int n_rng, int L, int K);
+ROSAR_API rosar_status rosar_sas_time_plan(const float *win, const rosar_c32 *w, const int32_t *o,
+                                           const rosar_radar *radar, int n_az, int L, int n_rng, int K, int centred,
+                                           void *plan, size_t plan_bytes, void *stream);
+ROSAR_API rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, const int32_t *o, int n_az, int L,
+                                              int n_rng, int K, rosar_c32 *out, void *stream);
+ROSAR_API rosar_status rosar_bpa_time_plan(const float *win, const rosar_radar *radar, int n_az, int L, int n_rng,
+                                           int M_ap, void *plan, size_t plan_bytes, void *stream);
+ROSAR_API rosar_status rosar_bpa_time_planned(const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng,
+                                              int M_ap, rosar_c32 *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Frequency-domain form of the sparse azimuth filter.  Eq. (43) with a fixed
  * row is a circular convolution of S[r][.] with g_r, g_r[(-o_k) mod n_az] += w[r][k];

@@ -16,6 +16,7 @@ from .ops import (MigratingPlan, azimuth_plan_migrating, image_migrating_fft,  #
                   sparse_azimuth_migrating_fft)
 from .ops import (azimuth_weight_grad_fft_phase, azimuth_weight_grad_spectra, phase_grad_phasor,  # noqa: F401
                   phasors, sparse_azimuth_fft_scans_ex)
+from .ops import TimeDomainPlan, bpa_time_plan, bpa_time_planned, sas_time_plan, sas_time_planned  # noqa: F401
 from .batch import Batch, Tuning  # noqa: F401
 from . import autograd, autotune  # noqa: F401
 

@@ -239,6 +239,112 @@ rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, const rosar_
                               static_cast<cudaStream_t>(stream));
 }
 
+size_t rosar_time_domain_plan_bytes(int n_rng, int L, int K) {
+    if (n_rng < 1 || L < 1 || K < 1) return 0;
+    return time_domain_plan_bytes(n_rng, L, K);
+}
+
+namespace {
+// Geometry of a plan call (the plan kernel reads no raw cube): the checks of time_domain_params without raw/out.
+rosar_status plan_params(const char *what, const rosar_radar *radar, int n_az, int L, int n_rng, int K, bool centred,
+                         const void *plan, size_t plan_bytes, TdParams *p) {
+    if (!radar || !plan) return set_error(ROSAR_ERR_INVALID_ARG, "%s: null radar or plan", what);
+    if (n_az < 1 || n_rng < 1 || K < 1 || L < 16 || L > 65536)
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: need n_az, n_rng, K >= 1 and 16 <= L <= 65536", what);
+    if (L % time_domain_sample_multiple() != 0)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: L=%d is not a multiple of %d", what, L, time_domain_sample_multiple());
+    if ((long long)n_rng * K > kMaxElems || (long long)n_rng * n_az > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: sizes too large", what);
+    if (plan_bytes < time_domain_plan_bytes(n_rng, L, K))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: plan of %zu bytes < %zu needed", what, plan_bytes,
+                         time_domain_plan_bytes(n_rng, L, K));
+    if (misaligned(plan, 16)) return set_error(ROSAR_ERR_INVALID_ARG, "%s: plan must be 16-byte aligned", what);
+    const double c = radar->c_mps > 0 ? radar->c_mps : 299792458.0;
+    if (!(radar->slope_hz_per_s > 0) || !(radar->t_sample_s > 0) || !(radar->r0_m >= 0) || !(radar->fc_hz > 0))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: radar parameters must be positive", what);
+    p->dR = c / (2.0 * radar->slope_hz_per_s * radar->t_sample_s * L);
+    const double f_mid = radar->fc_hz + radar->slope_hz_per_s * (radar->t_start_s + radar->t_sample_s * (L - 1) / 2.0);
+    p->two_f_over_c = 2.0 * f_mid / c;
+    p->phi_scale = 2.0 / (p->dR * L);
+    p->r0 = radar->r0_m;
+    p->m_ref = centred ? 0.5f * (float)(L - 1) : 0.f;
+    p->n_az = n_az;
+    p->L = L;
+    p->n_rng = n_rng;
+    return ROSAR_OK;
+}
+
+rosar_status planned_params(const char *what, const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng, int K,
+                            const rosar_c32 *out, TdParams *p) {
+    if (!raw || !plan || !out) return set_error(ROSAR_ERR_INVALID_ARG, "%s: null raw, plan or out", what);
+    if (n_az < 1 || n_rng < 1 || K < 1 || L < 16 || L > 65536)
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: need n_az, n_rng, K >= 1 and 16 <= L <= 65536", what);
+    if (L % time_domain_sample_multiple() != 0)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: L=%d is not a multiple of %d", what, L, time_domain_sample_multiple());
+    if ((long long)n_az * L > kMaxElems || (long long)n_rng * n_az > kMaxElems || (long long)n_rng * K > kMaxElems)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "%s: sizes too large", what);
+    if (misaligned(raw, 16) || misaligned(out, 8) || misaligned(plan, 16))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: misaligned pointer", what);
+    const size_t ob = sizeof(rosar_c32) * (size_t)n_rng * n_az;
+    if (overlaps(out, ob, raw, sizeof(rosar_c32) * (size_t)n_az * L) ||
+        overlaps(out, ob, plan, time_domain_plan_bytes(n_rng, L, K)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "%s: out overlaps raw or the plan", what);
+    *p = TdParams{};
+    p->n_az = n_az;
+    p->L = L;
+    p->n_rng = n_rng;
+    return ROSAR_OK;
+}
+}  // namespace
+
+rosar_status rosar_sas_time_plan(const float *win, const rosar_c32 *w, const int32_t *o, const rosar_radar *radar,
+                                 int n_az, int L, int n_rng, int K, int centred, void *plan, size_t plan_bytes,
+                                 void *stream) {
+    clear_error();
+    if (centred != 0 && centred != 1) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time_plan: centred must be 0 or 1");
+    if (!w || !o) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time_plan: null w or o");
+    TdParams p;
+    rosar_status st = plan_params("sas_time_plan", radar, n_az, L, n_rng, K, centred == 1, plan, plan_bytes, &p);
+    if (st != ROSAR_OK) return st;
+    if (misaligned(w, 8) || misaligned(o, 4) || (win && misaligned(win, 4)))
+        return set_error(ROSAR_ERR_INVALID_ARG, "sas_time_plan: misaligned pointer");
+    return launch_time_domain_plan(win, reinterpret_cast<const float2 *>(w), o, p, K, false, plan,
+                                   static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, const int32_t *o, int n_az, int L,
+                                    int n_rng, int K, rosar_c32 *out, void *stream) {
+    clear_error();
+    if (!o || misaligned(o, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time_planned: null or misaligned o");
+    TdParams p;
+    rosar_status st = planned_params("sas_time_planned", raw, plan, n_az, L, n_rng, K, out, &p);
+    if (st != ROSAR_OK) return st;
+    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), o, p, K, false, plan,
+                                      reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_bpa_time_plan(const float *win, const rosar_radar *radar, int n_az, int L, int n_rng, int M_ap,
+                                 void *plan, size_t plan_bytes, void *stream) {
+    clear_error();
+    TdParams p;
+    rosar_status st = plan_params("bpa_time_plan", radar, n_az, L, n_rng, M_ap, true, plan, plan_bytes, &p);
+    if (st != ROSAR_OK) return st;
+    if (M_ap > n_az) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time_plan: M_ap=%d exceeds n_az=%d", M_ap, n_az);
+    if (win && misaligned(win, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time_plan: misaligned win");
+    return launch_time_domain_plan(win, nullptr, nullptr, p, M_ap, true, plan, static_cast<cudaStream_t>(stream));
+}
+
+rosar_status rosar_bpa_time_planned(const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng, int M_ap,
+                                    rosar_c32 *out, void *stream) {
+    clear_error();
+    TdParams p;
+    rosar_status st = planned_params("bpa_time_planned", raw, plan, n_az, L, n_rng, M_ap, out, &p);
+    if (st != ROSAR_OK) return st;
+    if (M_ap > n_az) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time_planned: M_ap=%d exceeds n_az=%d", M_ap, n_az);
+    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), nullptr, p, M_ap, true, plan,
+                                      reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
+}
+
 rosar_status rosar_image(const rosar_c32 *raw, const float *win, const rosar_c32 *w, const int32_t *o,
                          int o_row_stride, int n_az, int L, int K, rosar_c32 *workspace, rosar_c32 *out, void *stream) {
     clear_error();

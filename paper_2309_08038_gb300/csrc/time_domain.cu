@@ -179,10 +179,14 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
 // where two warps refresh the per-(row, tap) table two taps ahead.  At the end of each period of PERIOD stages the
 // producers wait for the period's MMAs, fold X into Y and arrive on `fold`, which the issuer waits on before the
 // next period's first MMA overwrites X.
+// bplan (optional): the B operand precomputed by td_plan_kernel (coefficient x window x phasor of every (tap,
+// sample, row), split into bf16 hi and lo pairs): the producers then load and rearrange it instead of
+// generating it.
 template <bool BPA>
 __global__ void __launch_bounds__(tcg::THREADS, 2)
 td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
-             const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
+             const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out,
+             const uint4 *__restrict__ bplan) {
     using namespace tcg;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
@@ -238,7 +242,7 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         const float2 s1 = phasor_term(u, 1.f, 1.f), s16 = phasor_term(u, 1.f, (float)MC);
         stp[(kk % 3) * BR + j] = make_float4(s1.x, s1.y, s16.x, s16.y);
     };
-    if (warp < 2 && stages > 0) {
+    if (warp < 2 && stages > 0 && !bplan) {
         build_tab(0);
         if (nk > 1) build_tab(1);
     }
@@ -318,7 +322,13 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             if (s >= 2 && ok) ok = wait_bar(&empty[b], (uint32_t)(((s - 2) >> 1) & 1));
             if (m0 == 0) {                     // tap boundary: the table of tap kk-1 is no longer read
                 asm volatile("bar.sync 1, %0;" ::"n"(PRODUCERS) : "memory");
-                if (warp < 2 && kk + 2 < nk) build_tab(kk + 2);
+                if (warp < 2 && kk + 2 < nk && !bplan) build_tab(kk + 2);
+            }
+            uint4 pl_hi = make_uint4(0u, 0u, 0u, 0u), pl_lo = pl_hi;
+            if (bplan && r0 + b_r < p.n_rng) {      // this thread's 4 samples of row r0 + b_r: [tap][m / 4][row] x (hi, lo)
+                const uint4 *q4 = bplan + 2 * (((size_t)(k_lo + kk) * (L / 4) + (m0 / 4 + b_c)) * p.n_rng + r0 + b_r);
+                pl_hi = __ldg(q4);
+                pl_lo = __ldg(q4 + 1);
             }
             if (s + 1 < stages) {
                 prefetch_A(s + 1, m0 + MC == L ? kk + 1 : kk, m0 + MC == L ? 0 : m0 + MC);
@@ -340,7 +350,26 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             // B: thread = (row r = 8 warp + (lane & 7), samples 4 (lane >> 3) ..): coefficient x window x phasor by a
             // recurrence over the 4 samples, rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes with r & 4
             // write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
-            {
+            if (bplan) {
+                // (v.re, v.im) pairs of the plan: row (re) = (v.re, -v.im), row (im) = (v.im, v.re)
+                const uint32_t hv[4] = {pl_hi.x, pl_hi.y, pl_hi.z, pl_hi.w}, lv[4] = {pl_lo.x, pl_lo.y, pl_lo.z, pl_lo.w};
+                uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    re_hi[i] = hv[i] ^ 0x80000000u;
+                    re_lo[i] = lv[i] ^ 0x80000000u;
+                    im_hi[i] = __byte_perm(hv[i], 0, 0x1032);
+                    im_lo[i] = __byte_perm(lv[i], 0, 0x1032);
+                }
+                const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+                const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+                const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+                const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_first) = b_swap ? ih : rh;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_first) = b_swap ? il : rl;
+                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_second) = b_swap ? rh : ih;
+                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_second) = b_swap ? rl : il;
+            } else {
                 const int r = b_r;
                 const float4 t4 = tab[slot * BR + r];
                 const float4 st4 = stp[slot * BR + r];
@@ -468,6 +497,50 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     }
 }
 
+// The B operand of td_tc_kernel for every (tap, sample, row), computed once per weight design (a "plan"):
+// v = c * win[m] * exp(-j*pi*phi*(m - m_ref)) (tap_entry, phasor_term; each sample's phasor taken exactly rather
+// than by recurrence), split into bf16 hi and lo pairs (v.re, v.im) and stored [tap][m / 4][row] as the hi pairs
+// and the lo pairs of the 4 samples (32 bytes).  Grid (K, row blocks of TP_ROWS), 256 threads.
+constexpr int TP_ROWS = 64;
+template <bool BPA>
+__global__ void __launch_bounds__(256)
+td_plan_kernel(const float *__restrict__ win, const float2 *__restrict__ w, const int32_t *__restrict__ o, TdParams p,
+               int K, uint4 *__restrict__ plan) {
+    __shared__ float4 tab[TP_ROWS];
+    const int k = blockIdx.x, r0 = blockIdx.y * TP_ROWS;
+    const int off = BPA ? k - K / 2 : pmod(__ldg(o + k), p.n_az);
+    if (threadIdx.x < TP_ROWS) {
+        const int r = r0 + threadIdx.x;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < p.n_rng) {
+            t = tap_entry<BPA>(p, r, off);
+            if (!BPA) {
+                const float2 c = __ldg(w + (size_t)r * K + k);
+                t.x = c.x;
+                t.y = c.y;
+            }
+        }
+        tab[threadIdx.x] = t;
+    }
+    __syncthreads();
+    const int groups = p.L / 4;
+    for (int v = threadIdx.x; v < TP_ROWS * groups; v += blockDim.x) {
+        const int j = v % TP_ROWS, g = v / TP_ROWS;
+        const int r = r0 + j;
+        if (r >= p.n_rng) continue;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = 4 * g + i;
+            const float2 val = phasor_term(tab[j], win ? __ldg(win + m) : 1.f, (float)m - p.m_ref);
+            tcg::split2(val.x, val.y, hi[i], lo[i]);
+        }
+        uint4 *q = plan + 2 * (((size_t)k * groups + g) * p.n_rng + r);
+        q[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        q[1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
 // Per-row offsets: one CTA per (row, block of TR_BT pixels), two pixels per thread.  Samples are taken in
 // chunks of TR_MC: the row's B chunk (all taps x TR_MC samples; one sincospif each) is generated into
 // shared memory, then every thread sweeps taps and samples, reading its pulses' samples as float4 pairs.
@@ -585,7 +658,7 @@ int pick_cluster_tc(int tiles, int K) {
 
 template <bool BPA>
 rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
-                       float2 *out, cudaStream_t s) {
+                       float2 *out, cudaStream_t s, const uint4 *bplan = nullptr) {
     static int done[kMaxDevices] = {};
     rosar_status st = ensure_smem((const void *)td_tc_kernel<BPA>, tcg::SMEM, done, BPA ? "bpa_time" : "sas_time");
     if (st != ROSAR_OK) return st;
@@ -604,7 +677,7 @@ rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, con
     attr[0].val.clusterDim.z = G;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tc_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tc_kernel<BPA>, raw, win, w, o, p, K, k_per, out, bplan);
     if (e != cudaSuccess)
         return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", BPA ? "bpa_time" : "sas_time", cudaGetErrorString(e));
     return check_launch(BPA ? "bpa_time" : "sas_time");
@@ -613,6 +686,29 @@ rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, con
 }  // namespace
 
 int time_domain_sample_multiple() { return TD_MC; }
+
+size_t time_domain_plan_bytes(int n_rng, int L, int K) { return (size_t)8 * (size_t)n_rng * (size_t)L * (size_t)K; }
+
+rosar_status launch_time_domain_plan(const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
+                                     bool bpa, void *plan, cudaStream_t s) {
+    if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain plan: L=%d is not a multiple of %d", p.L, TD_MC);
+    const int gy = (p.n_rng + TP_ROWS - 1) / TP_ROWS;
+    if (gy > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain plan: n_rng=%d too large", p.n_rng);
+    dim3 grid(K, gy);
+    if (bpa) td_plan_kernel<true><<<grid, 256, 0, s>>>(win, w, o, p, K, static_cast<uint4 *>(plan));
+    else td_plan_kernel<false><<<grid, 256, 0, s>>>(win, w, o, p, K, static_cast<uint4 *>(plan));
+    return check_launch(bpa ? "bpa_time_plan" : "sas_time_plan");
+}
+
+rosar_status launch_time_domain_planned(const float2 *raw, const int32_t *o, const TdParams &p, int K, bool bpa,
+                                        const void *plan, float2 *out, cudaStream_t s) {
+    if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: L=%d is not a multiple of %d", p.L, TD_MC);
+    if ((p.n_rng + tcg::BR - 1) / tcg::BR > 65535)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
+    const uint4 *bp = static_cast<const uint4 *>(plan);
+    return bpa ? launch_tc<true>(raw, nullptr, nullptr, nullptr, p, K, out, s, bp)
+               : launch_tc<false>(raw, nullptr, nullptr, o, p, K, out, s, bp);
+}
 
 rosar_status launch_time_domain(const float2 *raw, const float *win, const float2 *w, const int32_t *o,
                                 int o_row_stride, const TdParams &p, int K, bool bpa, float2 *out, cudaStream_t s) {

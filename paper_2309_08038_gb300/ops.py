@@ -170,6 +170,76 @@ def sas_time(raw, win, w, o, radar: Radar, centred=True, out=None, stream=None):
     return out
 
 
+@dataclass(frozen=True)
+class TimeDomainPlan:
+    """The precomputed B operand of the tensor-core time-domain forms (rosar_*_time_plan): a uint8 device tensor
+    of rosar_time_domain_plan_bytes(n_rng, L, K) bytes, with the shape it was made for."""
+
+    data: torch.Tensor
+    n_az: int
+    L: int
+    n_rng: int
+    K: int
+
+
+def _plan_tensor(n_rng, L, K, device):
+    nbytes = int(_lib.load().rosar_time_domain_plan_bytes(n_rng, L, K))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def sas_time_plan(win, w, o, radar: Radar, n_az, L, centred=True, stream=None):
+    """rosar_sas_time_plan: the B operand of rosar_sas_time for the weights w [n_rng, K] and shared offsets o [K]."""
+    lib = _lib.load()
+    require(w, torch.complex64, "w", ndim=2)
+    n_rng, K = w.shape
+    require(o, torch.int32, "o", shape=(K,))
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    data = _plan_tensor(n_rng, L, K, w.device)
+    st = radar.as_struct()
+    check(lib.rosar_sas_time_plan(ptr(win), ptr(w), ptr(o), ctypes.byref(st), n_az, L, n_rng, K, 1 if centred else 0,
+                                  ptr(data), data.numel(), stream_handle(stream)))
+    return TimeDomainPlan(data, n_az, L, n_rng, K)
+
+
+def sas_time_planned(raw, plan: TimeDomainPlan, o, out=None, stream=None):
+    """rosar_sas_time_planned: rosar_sas_time of raw [n_az, L] with a plan from sas_time_plan (same offsets o)."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", shape=(plan.n_az, plan.L))
+    require(o, torch.int32, "o", shape=(plan.K,))
+    if out is None:
+        out = torch.empty((plan.n_rng, plan.n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(plan.n_rng, plan.n_az))
+    check(lib.rosar_sas_time_planned(ptr(raw), ptr(plan.data), ptr(o), plan.n_az, plan.L, plan.n_rng, plan.K, ptr(out),
+                                     stream_handle(stream)))
+    return out
+
+
+def bpa_time_plan(win, radar: Radar, n_az, L, n_rng, M_ap, device=None, stream=None):
+    """rosar_bpa_time_plan: the B operand of rosar_bpa_time (M_ap taps of the nominal geometry)."""
+    lib = _lib.load()
+    if win is not None:
+        require(win, torch.float32, "win", shape=(L,))
+    device = win.device if win is not None else (device or torch.device("cuda"))
+    data = _plan_tensor(n_rng, L, M_ap, device)
+    st = radar.as_struct()
+    check(lib.rosar_bpa_time_plan(ptr(win), ctypes.byref(st), n_az, L, n_rng, M_ap, ptr(data), data.numel(),
+                                  stream_handle(stream)))
+    return TimeDomainPlan(data, n_az, L, n_rng, M_ap)
+
+
+def bpa_time_planned(raw, plan: TimeDomainPlan, out=None, stream=None):
+    """rosar_bpa_time_planned: rosar_bpa_time of raw [n_az, L] with a plan from bpa_time_plan."""
+    lib = _lib.load()
+    require(raw, torch.complex64, "raw", shape=(plan.n_az, plan.L))
+    if out is None:
+        out = torch.empty((plan.n_rng, plan.n_az), dtype=torch.complex64, device=raw.device)
+    require(out, torch.complex64, "out", shape=(plan.n_rng, plan.n_az))
+    check(lib.rosar_bpa_time_planned(ptr(raw), ptr(plan.data), plan.n_az, plan.L, plan.n_rng, plan.K, ptr(out),
+                                     stream_handle(stream)))
+    return out
+
+
 def image(raw, win, w, o, workspace=None, out=None, stream=None):
     """rosar_image: range compression into `workspace`, then the sparse azimuth filter into `out`."""
     lib = _lib.load()

@@ -230,3 +230,18 @@ def test_fused_phase_calls_reject_bad_arguments(lib):
     assert lib.rosar_azimuth_weight_grad_spectra(FAKE, FAKE2, FAKE3, 0, 2, 4, 3600, 8, FAKE, FAKE3, None) == 1  # ws = G
     assert lib.rosar_azimuth_weight_grad_fft_phase(FAKE, FAKE2, None, FAKE3, 0, 2, 4, 3600, 8, FAKE3, None) == 1
     assert lib.rosar_phase_grad_phasor(FAKE, FAKE2, FAKE3, 2, 4, 3600, None, None, None) == 1   # nothing to compute
+
+
+def test_time_domain_plans_reject_bad_arguments(lib):
+    from paper_2309_08038_gb300 import _lib as L
+    rad = L.RadarStruct(77e9, 1e14, 1e-7, 8e-6, 0.25, 0.0)
+    FAKE3 = ctypes.c_void_p(0x30000000)
+    n = lib.rosar_time_domain_plan_bytes(64, 64, 16)
+    assert n == 8 * 64 * 64 * 16
+    assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 64, 64, 16, 1, FAKE3, n - 1, None) == 1
+    assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 48 + 2, 64, 16, 1, FAKE3, n, None) == 2
+    assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 64, 64, 16, 1, ctypes.c_void_p(0x30000008),
+                                   n, None) == 1                                        # plan not 16-byte aligned
+    assert lib.rosar_bpa_time_plan(None, ctypes.byref(rad), 360, 64, 64, 361, FAKE3, 8 * 64 * 64 * 361, None) == 1
+    assert lib.rosar_sas_time_planned(FAKE, FAKE3, None, 360, 64, 64, 16, FAKE2, None) == 1      # null o
+    assert lib.rosar_bpa_time_planned(FAKE, FAKE3, 360, 64, 64, 60, FAKE, None) == 1            # out aliases raw

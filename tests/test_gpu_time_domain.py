@@ -134,3 +134,62 @@ def test_time_domain_full_size_sampled_pixels(rosar, torch, name):
     sel = slice(0, 12)
     ref = O.bpa_time_pixels(sc.raw, win, o_rad, cfg.n_az, cfg.M_ap, rows[sel], thetas[sel])
     assert rel_l2(bpa[rows[sel], thetas[sel]], ref) <= TOL
+
+
+# ------------------------------------------------------ planned forms (B operand precomputed) --
+
+@pytest.mark.parametrize("centred", [True, False])
+def test_sas_time_planned_matches_oracle_and_unplanned(rosar, torch, centred):
+    """The plan (coefficient x window x phasor of every tap, sample and row, split into bf16 pairs) fed to the
+    tensor-core kernel: the tiny image against the oracle, and equal to the unplanned call within the
+    tolerance; a second scan through the same plan."""
+    cfg = synth.TINY
+    sc = scene("tiny")
+    w, o = _weights(cfg)
+    win = dev(torch, synth.hann_window(cfg.L))
+    plan = rosar.sas_time_plan(win, dev(torch, w), dev(torch, o), api_radar(rosar, cfg), cfg.n_az, cfg.L,
+                               centred=centred)
+    assert plan.data.numel() == 8 * cfg.L * cfg.L * cfg.K
+    ref = O.sas_time(sc.raw, synth.hann_window(cfg.L), w, o, oracle_radar(cfg), cfg.L, centred=centred)
+    got = host(rosar.sas_time_planned(dev(torch, sc.raw), plan, dev(torch, o)))
+    assert rel_l2(got, ref) <= TOL
+    unplanned = host(rosar.sas_time(dev(torch, sc.raw), win, dev(torch, w), dev(torch, o), api_radar(rosar, cfg),
+                                    centred=centred))
+    assert rel_l2(got, unplanned) <= TOL
+    raw2 = np.roll(sc.raw, 41, axis=0)
+    got2 = host(rosar.sas_time_planned(dev(torch, raw2), plan, dev(torch, o)))
+    assert rel_l2(got2, np.roll(ref, 41, axis=1)) <= TOL
+
+
+@pytest.mark.parametrize("n_az,L,n_rng,M_ap", [(200, 48, 45, 13), (97, 32, 1, 97), (360, 64, 64, 60)])
+def test_bpa_time_planned_ragged(rosar, torch, n_az, L, n_rng, M_ap):
+    """Planned time-domain BPA on ragged tiles (rows and azimuth off the tile, L a multiple of 16 but not a
+    power of two, one row, the whole ring) against the oracle."""
+    o_rad, a_rad = _radar_pair(rosar, L)
+    rng = np.random.default_rng(n_az + 3 * L)
+    raw = crand(rng, n_az, L)
+    win = rng.uniform(0.1, 1.0, L).astype(np.float32)
+    plan = rosar.bpa_time_plan(dev(torch, win), a_rad, n_az, L, n_rng, M_ap)
+    got = host(rosar.bpa_time_planned(dev(torch, raw), plan))
+    assert rel_l2(got, O.bpa_time(raw, win, o_rad, n_rng, M_ap)) <= TOL
+
+
+def test_time_domain_planned_full_size_sampled_pixels(rosar, torch):
+    """The indoor workload through the planned kernels in the benchmark's launch configuration, sampled pixels
+    against the oracle."""
+    cfg = synth.INDOOR
+    sc = scene("indoor")
+    w, o = _weights(cfg)
+    win = synth.hann_window(cfg.L)
+    o_rad = oracle_radar(cfg)
+    rng = np.random.default_rng(43)
+    rows = np.concatenate([rng.integers(1, cfg.L, 20), [cfg.L - 1]])
+    thetas = np.concatenate([rng.integers(0, cfg.n_az, 20), [cfg.n_az - 1]])
+    plan = rosar.sas_time_plan(dev(torch, win), dev(torch, w), dev(torch, o), api_radar(rosar, cfg), cfg.n_az, cfg.L)
+    sas = host(rosar.sas_time_planned(dev(torch, sc.raw), plan, dev(torch, o)))
+    assert rel_l2(sas[rows, thetas], O.sas_time_pixels(sc.raw, win, w, o, o_rad, cfg.n_az, rows, thetas)) <= TOL
+    bplan = rosar.bpa_time_plan(dev(torch, win), api_radar(rosar, cfg), cfg.n_az, cfg.L, cfg.L, cfg.M_ap)
+    bpa = host(rosar.bpa_time_planned(dev(torch, sc.raw), bplan))
+    sel = slice(0, 10)
+    ref = O.bpa_time_pixels(sc.raw, win, o_rad, cfg.n_az, cfg.M_ap, rows[sel], thetas[sel])
+    assert rel_l2(bpa[rows[sel], thetas[sel]], ref) <= TOL
