@@ -236,19 +236,23 @@ ROSAR_API rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, co
  * geometry, the window and the weights, not on the raw cube, so a caller imaging many scans with one design
  * computes it once; each planned call then only streams the raw cube through the tensor cores.  Same sums
  * as rosar_bpa_time / rosar_sas_time (shared offsets), each sample's phasor taken directly instead of by
- * recurrence (float32 rounding differs).
- *   rosar_time_domain_plan_bytes: size of a plan, 8 * n_rng * L * K bytes (K = M_ap for BPA).
+ * recurrence (float32 rounding differs).  The plan holds the taps in ascending offset order (with their
+ * offsets), tiled as the tensor cores read them; the planned call sums the taps in that order, and taps whose
+ * offsets lie within 120 pulses of each other share one staged window of raw pulses.
+ *   rosar_time_domain_plan_bytes: size of a plan, 16384 * ceil(n_rng / 64) * K * (L / 16) + 8 * K bytes
+ *     (rounded up to 16; K = M_ap for BPA).
  *   rosar_sas_time_plan / rosar_bpa_time_plan: write the plan (device, 16-byte aligned, >= the size above);
- *     arguments as rosar_sas_time (shared offsets o [K]) / rosar_bpa_time.
- *   rosar_sas_time_planned / rosar_bpa_time_planned: the image from raw [n_az][L] with the plan; o is the
- *     plan's offsets [K].  Limits as the unplanned calls.
+ *     arguments as rosar_sas_time (shared offsets o [K], any int32 values) / rosar_bpa_time.
+ *   rosar_sas_time_planned / rosar_bpa_time_planned: the image from raw [n_az][L] (device, 16-byte aligned)
+ *     with the plan (read only; n_az, L, n_rng and K as given to the plan call).  Limits as the unplanned
+ *     calls, and ceil(n_rng / 64) <= 65535, K <= 65535.
  */
 ROSAR_API size_t rosar_time_domain_plan_bytes(int n_rng, int L, int K);
 ROSAR_API rosar_status rosar_sas_time_plan(const float *win, const rosar_c32 *w, const int32_t *o,
                                            const rosar_radar *radar, int n_az, int L, int n_rng, int K, int centred,
                                            void *plan, size_t plan_bytes, void *stream);
-ROSAR_API rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, const int32_t *o, int n_az, int L,
-                                              int n_rng, int K, rosar_c32 *out, void *stream);
+ROSAR_API rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng,
+                                              int K, rosar_c32 *out, void *stream);
 ROSAR_API rosar_status rosar_bpa_time_plan(const float *win, const rosar_radar *radar, int n_az, int L, int n_rng,
                                            int M_ap, void *plan, size_t plan_bytes, void *stream);
 ROSAR_API rosar_status rosar_bpa_time_planned(const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng,

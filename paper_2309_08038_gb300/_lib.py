@@ -70,7 +70,7 @@ _PROTOS = {
     "rosar_phase_grad_phasor": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "rosar_time_domain_plan_bytes": (ctypes.c_size_t, [_I, _I, _I]),
     "rosar_sas_time_plan": (_I, [_P, _P, _P, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _I, _P, ctypes.c_size_t, _P]),
-    "rosar_sas_time_planned": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
+    "rosar_sas_time_planned": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_bpa_time_plan": (_I, [_P, ctypes.POINTER(RadarStruct), _I, _I, _I, _I, _P, ctypes.c_size_t, _P]),
     "rosar_bpa_time_planned": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "rosar_azimuth_plan_migrating": (_I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),

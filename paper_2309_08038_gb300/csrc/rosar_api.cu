@@ -312,14 +312,13 @@ rosar_status rosar_sas_time_plan(const float *win, const rosar_c32 *w, const int
                                    static_cast<cudaStream_t>(stream));
 }
 
-rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, const int32_t *o, int n_az, int L,
-                                    int n_rng, int K, rosar_c32 *out, void *stream) {
+rosar_status rosar_sas_time_planned(const rosar_c32 *raw, const void *plan, int n_az, int L, int n_rng, int K,
+                                    rosar_c32 *out, void *stream) {
     clear_error();
-    if (!o || misaligned(o, 4)) return set_error(ROSAR_ERR_INVALID_ARG, "sas_time_planned: null or misaligned o");
     TdParams p;
     rosar_status st = planned_params("sas_time_planned", raw, plan, n_az, L, n_rng, K, out, &p);
     if (st != ROSAR_OK) return st;
-    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), o, p, K, false, plan,
+    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), p, K, false, plan,
                                       reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
 }
 
@@ -341,7 +340,7 @@ rosar_status rosar_bpa_time_planned(const rosar_c32 *raw, const void *plan, int 
     rosar_status st = planned_params("bpa_time_planned", raw, plan, n_az, L, n_rng, M_ap, out, &p);
     if (st != ROSAR_OK) return st;
     if (M_ap > n_az) return set_error(ROSAR_ERR_INVALID_ARG, "bpa_time_planned: M_ap=%d exceeds n_az=%d", M_ap, n_az);
-    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), nullptr, p, M_ap, true, plan,
+    return launch_time_domain_planned(reinterpret_cast<const float2 *>(raw), p, M_ap, true, plan,
                                       reinterpret_cast<float2 *>(out), static_cast<cudaStream_t>(stream));
 }
 

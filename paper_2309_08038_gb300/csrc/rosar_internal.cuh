@@ -157,12 +157,13 @@ struct TdParams {
 int time_domain_sample_multiple();
 rosar_status launch_time_domain(const float2 *raw, const float *win, const float2 *w, const int32_t *o,
                                 int o_row_stride, const TdParams &p, int K, bool bpa, float2 *out, cudaStream_t s);
-// The precomputed B operand of the tensor-core form (shared offsets): plan bytes, the plan kernel, the planned call.
+// The precomputed B operand of the tensor-core form (shared offsets; taps sorted by offset, the sorted offsets kept
+// in the plan): plan bytes, the plan kernels, the planned call.
 size_t time_domain_plan_bytes(int n_rng, int L, int K);
 rosar_status launch_time_domain_plan(const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
                                      bool bpa, void *plan, cudaStream_t s);
-rosar_status launch_time_domain_planned(const float2 *raw, const int32_t *o, const TdParams &p, int K, bool bpa,
-                                        const void *plan, float2 *out, cudaStream_t s);
+rosar_status launch_time_domain_planned(const float2 *raw, const TdParams &p, int K, bool bpa, const void *plan,
+                                        float2 *out, cudaStream_t s);
 
 rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, const float *dr, int L, int n_rng,
                         int n_az, int M_ap, int interp, float2 *out, cudaStream_t s);

@@ -179,14 +179,10 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
 // where two warps refresh the per-(row, tap) table two taps ahead.  At the end of each period of PERIOD stages the
 // producers wait for the period's MMAs, fold X into Y and arrive on `fold`, which the issuer waits on before the
 // next period's first MMA overwrites X.
-// bplan (optional): the B operand precomputed by td_plan_kernel (coefficient x window x phasor of every (tap,
-// sample, row), split into bf16 hi and lo pairs): the producers then load and rearrange it instead of
-// generating it.
 template <bool BPA>
 __global__ void __launch_bounds__(tcg::THREADS, 2)
 td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
-             const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out,
-             const uint4 *__restrict__ bplan) {
+             const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
     using namespace tcg;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *stage_base = smem;                                  // [2][A hi, A lo, B hi, B lo]
@@ -242,7 +238,7 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
         const float2 s1 = phasor_term(u, 1.f, 1.f), s16 = phasor_term(u, 1.f, (float)MC);
         stp[(kk % 3) * BR + j] = make_float4(s1.x, s1.y, s16.x, s16.y);
     };
-    if (warp < 2 && stages > 0 && !bplan) {
+    if (warp < 2 && stages > 0) {
         build_tab(0);
         if (nk > 1) build_tab(1);
     }
@@ -322,13 +318,7 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             if (s >= 2 && ok) ok = wait_bar(&empty[b], (uint32_t)(((s - 2) >> 1) & 1));
             if (m0 == 0) {                     // tap boundary: the table of tap kk-1 is no longer read
                 asm volatile("bar.sync 1, %0;" ::"n"(PRODUCERS) : "memory");
-                if (warp < 2 && kk + 2 < nk && !bplan) build_tab(kk + 2);
-            }
-            uint4 pl_hi = make_uint4(0u, 0u, 0u, 0u), pl_lo = pl_hi;
-            if (bplan && r0 + b_r < p.n_rng) {      // this thread's 4 samples of row r0 + b_r: [tap][m / 4][row] x (hi, lo)
-                const uint4 *q4 = bplan + 2 * (((size_t)(k_lo + kk) * (L / 4) + (m0 / 4 + b_c)) * p.n_rng + r0 + b_r);
-                pl_hi = __ldg(q4);
-                pl_lo = __ldg(q4 + 1);
+                if (warp < 2 && kk + 2 < nk) build_tab(kk + 2);
             }
             if (s + 1 < stages) {
                 prefetch_A(s + 1, m0 + MC == L ? kk + 1 : kk, m0 + MC == L ? 0 : m0 + MC);
@@ -350,26 +340,7 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
             // B: thread = (row r = 8 warp + (lane & 7), samples 4 (lane >> 3) ..): coefficient x window x phasor by a
             // recurrence over the 4 samples, rows (r, re) = [b.re, -b.im] and (r, im) = [b.im, b.re]; lanes with r & 4
             // write the im row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
-            if (bplan) {
-                // (v.re, v.im) pairs of the plan: row (re) = (v.re, -v.im), row (im) = (v.im, v.re)
-                const uint32_t hv[4] = {pl_hi.x, pl_hi.y, pl_hi.z, pl_hi.w}, lv[4] = {pl_lo.x, pl_lo.y, pl_lo.z, pl_lo.w};
-                uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    re_hi[i] = hv[i] ^ 0x80000000u;
-                    re_lo[i] = lv[i] ^ 0x80000000u;
-                    im_hi[i] = __byte_perm(hv[i], 0, 0x1032);
-                    im_lo[i] = __byte_perm(lv[i], 0, 0x1032);
-                }
-                const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
-                const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
-                const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
-                const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
-                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_first) = b_swap ? ih : rh;
-                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_first) = b_swap ? il : rl;
-                *reinterpret_cast<uint4 *>(st + 2 * TILE + b_second) = b_swap ? rh : ih;
-                *reinterpret_cast<uint4 *>(st + 3 * TILE + b_second) = b_swap ? rl : il;
-            } else {
+            {
                 const int r = b_r;
                 const float4 t4 = tab[slot * BR + r];
                 const float4 st4 = stp[slot * BR + r];
@@ -497,48 +468,352 @@ td_tc_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const 
     }
 }
 
-// The B operand of td_tc_kernel for every (tap, sample, row), computed once per weight design (a "plan"):
-// v = c * win[m] * exp(-j*pi*phi*(m - m_ref)) (tap_entry, phasor_term; each sample's phasor taken exactly rather
-// than by recurrence), split into bf16 hi and lo pairs (v.re, v.im) and stored [tap][m / 4][row] as the hi pairs
-// and the lo pairs of the 4 samples (32 bytes).  Grid (K, row blocks of TP_ROWS), 256 threads.
-constexpr int TP_ROWS = 64;
+// ------------------------------------------------------------ planned tensor-core form (sliding A window) --
+// With the B operand prepared once per weight design the A operand becomes the only per-scan input, and it is
+// shared between taps: the A tile of tap k is the raw pulses th0 + o_k + t (t < 128), so taps whose offsets lie
+// within a span d of each other read rows of ONE window of 128 + d pulses.  In the no-swizzle K-major layout with
+// 8-row groups 128 B apart (rows 16 B apart throughout), the tile of tap k is that window from row o_k - o_first:
+// a start address 16 (o_k - o_first) bytes further on, same descriptor otherwise.  The loop runs sample chunks
+// outermost and the taps (sorted by offset, cut into segments whose span fits the window) inside: per chunk and
+// segment the producer warps stage one window (raw fp32 split into bf16 hi and lo), and per (chunk, tap) one thread
+// copies the planned B block (16 KB: hi tile then lo tile, canonical layout) with one bulk copy completing on the
+// stage's mbarrier.  A costs 128 + d rows per chunk and segment instead of 128 per chunk and tap.
+namespace tcw {
+using namespace tcg;
+constexpr int NS = 3;                              // B stage buffers
+constexpr int WMAX = 248;                          // window rows: 128 pixels + the segment's offset span
+constexpr int SPAN = WMAX - BT;                    // largest offset span of one segment
+constexpr int ALBO = WMAX * 16 + 64;               // K-adjacent core matrices of the window (+64 B: the four
+                                                   // 16-byte groups of a window store fall in distinct banks)
+constexpr int ASBO = 128;                          // 8-row groups of the window
+constexpr int APLANE = 4 * ALBO;                   // hi plane, then lo plane
+constexpr int WSLOT = 2 * APLANE;
+constexpr int BTILE = 2 * TILE;                    // planned B block (hi, lo)
+constexpr int THREADS = PRODUCERS + 64;            // warps 0-7 windows / fold / epilogue, 8 MMA issuer, 9 B copies
+constexpr int SMEM = NS * BTILE + 2 * WSLOT + 128; // + mbarriers and the TMEM slot
+static_assert(SMEM <= 232448 / 2 - 1024, "two CTAs per SM");
+static_assert(BT * NN * 4 <= NS * BTILE + 2 * WSLOT, "the cluster reduction parks a tile in the stage buffers");
+
+__device__ __forceinline__ uint64_t descA(uint32_t a) {
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(ALBO >> 4) << 16) | ((uint64_t)(ASBO >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+}  // namespace tcw
+
+template <bool BPA>
+__global__ void __launch_bounds__(tcw::THREADS, 2)
+td_tcw_kernel(const float2 *__restrict__ X, const uint8_t *__restrict__ Bt, const int32_t *__restrict__ offs,
+              TdParams p, int K, int k_per, float2 *__restrict__ out) {
+    using namespace tcw;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *bstage = smem;                                      // [NS][B hi, B lo]
+    uint8_t *wbase = smem + NS * BTILE;                          // [2][hi, lo][4 groups][ALBO]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * BTILE + 2 * WSLOT);
+    uint64_t *full = bars, *empty = bars + NS, *wfull = bars + 2 * NS, *wempty = bars + 2 * NS + 2,
+             *fold_bar = bars + 2 * NS + 4, *acc_bar = bars + 2 * NS + 5;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 6);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp < PRODUCERS / 32;
+    const int th0 = blockIdx.x * BT, rb = blockIdx.y, r0 = rb * BR;
+    const int n_az = p.n_az, L = p.L;
+    const int chunks = L / MC;
+    const int k_lo = blockIdx.z * k_per;
+    const int k_end = min(K, k_lo + k_per);
+    const int nk = max(0, k_end - k_lo);
+    const int stages = nk * chunks;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&empty[i])), "r"(1));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&wfull[i])), "r"(PRODUCERS / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&wempty[i])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(fold_bar)), "r"(PRODUCERS / 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(acc_bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    const uint32_t x_ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
+    // The producer warps do not follow every stage, so they learn that a period's MMAs are done from acc_bar (one
+    // phase per period end and one at the last stage, each waited for in order); a parity wait on a stage's
+    // `empty` barrier could match a later phase.
+    const uint32_t y_ta = x_ta + (uint32_t)NN;
+    bool have_y = false;
+    bool ok = true;
+
+    // segment of taps starting at ka: the longest run of (sorted) taps within SPAN of offs[ka]
+    auto seg_end = [&](int ka) {
+        const long long base = __ldg(offs + ka);
+        int kb = ka + 1;
+        while (kb < k_end && (long long)__ldg(offs + kb) - base <= SPAN) ++kb;
+        return kb;
+    };
+
+    if (producer) {
+        // window stores: thread = (sample pair a_j of the chunk, rows a_r + 32 i); a warp stores 4 rows x 8 pairs
+        const int a_j = tid & 7, a_r = tid >> 3;
+        const int a_dst = (a_j >> 1) * ALBO + (a_j & 1) * 8;
+        auto produce = [&](int w, int c, int ka, int kb) {
+            const int slot = w & 1;
+            if (w >= 2 && ok) ok = wait_bar(&wempty[slot], (uint32_t)(((w >> 1) - 1) & 1));
+            const int W = (int)((long long)__ldg(offs + kb - 1) - __ldg(offs + ka)) + BT;
+            const int p0 = pmod(th0 + pmod(__ldg(offs + ka), n_az), n_az);
+            uint8_t *ws = wbase + slot * WSLOT + a_dst;
+            const float2 *col = X + c * MC + 2 * a_j;
+#pragma unroll 2
+            for (int i = a_r; i < W; i += PRODUCERS / 8) {
+                int pulse = p0 + i;
+                if (pulse >= n_az) pulse %= n_az;
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(col + (size_t)pulse * L));
+                uint2 hi, lo;
+                split2(v.x, v.y, hi.x, lo.x);
+                split2(v.z, v.w, hi.y, lo.y);
+                *reinterpret_cast<uint2 *>(ws + 16 * i) = hi;
+                *reinterpret_cast<uint2 *>(ws + APLANE + 16 * i) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&wfull[slot])) : "memory");
+        };
+        auto fold = [&]() {                   // Y (+)= X, this warp's 32 lanes x 64 columns
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float xv[16], yv[16];
+                ld16(x_ta + 16 * c, xv);
+                if (have_y) {
+                    ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) xv[j] += yv[j];
+                }
+                st16(y_ta + 16 * c, xv);
+            }
+            have_y = true;
+        };
+        if (stages > 0) {
+            // windows are staged one ahead: window w + 1 is written (after window w - 1's MMAs released its slot)
+            // before the folds that fall inside window w's stages
+            int c_cur = 0, ka_cur = k_lo, kb_cur = seg_end(k_lo);
+            produce(0, 0, ka_cur, kb_cur);
+            int s = 0;
+            for (int w = 0;; ++w) {
+                int c_n = c_cur, ka_n = kb_cur, kb_n = 0;
+                if (ka_n == k_end) {
+                    ka_n = k_lo;
+                    ++c_n;
+                }
+                if (c_n < chunks) {
+                    kb_n = seg_end(ka_n);
+                    produce(w + 1, c_n, ka_n, kb_n);
+                }
+                const int s_end = s + (kb_cur - ka_cur);
+                // period ends inside this window: s + 1 a multiple of PERIOD, not the last stage
+                for (int se = ((s + PERIOD) / PERIOD) * PERIOD - 1; se < s_end && se + 1 < stages; se += PERIOD) {
+                    if (ok) ok = wait_bar(acc_bar, (uint32_t)((se / PERIOD) & 1));
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (ok) fold();
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(fold_bar)) : "memory");
+                }
+                s = s_end;
+                if (c_n >= chunks) break;
+                c_cur = c_n;
+                ka_cur = ka_n;
+                kb_cur = kb_n;
+            }
+            if (ok) ok = wait_bar(acc_bar, (uint32_t)(((stages - 1) / PERIOD) & 1));
+        }
+    } else if (warp == PRODUCERS / 32) {
+        if (lane == 0) {                      // the MMA issuer
+            int s = 0, w = 0;
+            for (int c = 0; c < chunks && ok; ++c) {
+                for (int ka = k_lo; ka < k_end && ok;) {
+                    const int kb = seg_end(ka);
+                    const int slot = w & 1;
+                    ok = wait_bar(&wfull[slot], (uint32_t)((w >> 1) & 1));
+                    if (!ok) break;
+                    const long long base = __ldg(offs + ka);
+                    const uint32_t wa = saddr(wbase + slot * WSLOT);
+                    for (int k = ka; k < kb; ++k, ++s) {
+                        const int b = s % NS;
+                        ok = wait_bar(&full[b], (uint32_t)((s / NS) & 1));
+                        if (ok && s % PERIOD == 0 && s > 0) ok = wait_bar(fold_bar, (uint32_t)((s / PERIOD - 1) & 1));
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a_hi = wa + (uint32_t)(((long long)__ldg(offs + k) - base) * 16),
+                                       a_lo = a_hi + APLANE;
+                        const uint32_t b_hi = saddr(bstage + b * BTILE), b_lo = b_hi + TILE;
+#pragma unroll
+                        for (int ks = 0; ks < KR / 16; ++ks) {
+                            const uint32_t ka2 = ks * 2 * ALBO, kb2 = ks * 2 * LBO;
+                            mma(tmem, descA(a_hi + ka2), desc(b_hi + kb2), (s % PERIOD != 0 || ks > 0) ? 1u : 0u);
+                            mma(tmem, descA(a_hi + ka2), desc(b_lo + kb2), 1u);
+                            mma(tmem, descA(a_lo + ka2), desc(b_hi + kb2), 1u);
+                        }
+                        commit(&empty[b]);
+                        if ((s + 1) % PERIOD == 0 || s + 1 == stages) commit(acc_bar);
+                    }
+                    if (!ok) break;
+                    if (c + 1 < chunks || kb < k_end) commit(&wempty[slot]);   // (the last window's slot is not reused)
+                    ++w;
+                    ka = kb;
+                }
+            }
+        }
+    } else if (lane == 0) {                   // the B copies: stage s = (chunk, tap) in the issuer's order
+        int s = 0;
+        for (int c = 0; c < chunks && ok; ++c) {
+            for (int k = k_lo; k < k_end; ++k, ++s) {
+                const int b = s % NS;
+                if (s >= NS) ok = wait_bar(&empty[b], (uint32_t)(((s / NS) - 1) & 1));
+                if (!ok) break;
+                const uint8_t *src = Bt + (((size_t)rb * K + k) * chunks + c) * BTILE;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[b])),
+                             "r"(BTILE) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(saddr(bstage + b * BTILE)), "l"(src), "r"(BTILE), "r"(saddr(&full[b])) : "memory");
+            }
+        }
+        // the copies of the last (up to NS) issued stages may still be in flight if a wait gave up: their
+        // completion is the only arrival their phase needs (bounded waits)
+        for (int s2 = max(0, s - NS); s2 < s; ++s2) wait_bar(&full[s2 % NS], (uint32_t)((s2 / NS) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    const int th = 32 * q + lane;
+    float v[64];
+    if (producer) {
+        if (ok && stages > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ld16(x_ta + 16 * c, v + 16 * c);
+                if (have_y) {
+                    float yv[16];
+                    ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[16 * c + j] += yv[j];
+                }
+            }
+        } else {
+            const float f = ok ? 0.f : __int_as_float(0x7fc00000);   // no taps: zero; a wait that gave up: NaN
+#pragma unroll
+            for (int j = 0; j < 64; ++j) v[j] = f;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+
+    const int G = gridDim.z;
+    bool writer = producer;
+    if (G > 1) {                              // partial tiles parked in the stage buffers, rank 0 adds in rank order
+        float *red = reinterpret_cast<float *>(smem);            // [128 columns][128 pixels] = 64 KB
+        cg::cluster_group cluster = cg::this_cluster();
+        if (producer) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) red[(64 * h + j) * BT + th] = v[j];
+        }
+        cluster.sync();
+        if (producer && cluster.block_rank() == 0) {
+            for (int rk = 1; rk < G; ++rk) {
+                const float *rem = cluster.map_shared_rank(red, rk);
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] += rem[(64 * h + j) * BT + th];
+            }
+        }
+        cluster.sync();
+        writer = producer && cluster.block_rank() == 0;
+    }
+    const int tcol = th0 + th;
+    if (writer && tcol < n_az) {
+#pragma unroll
+        for (int j = 0; j < 64; j += 2) {
+            const int r = r0 + (64 * h + j) / 2;
+            if (r < p.n_rng) out[(size_t)r * n_az + tcol] = make_float2(v[j], v[j + 1]);
+        }
+    }
+}
+
+// Taps in ascending offset order (ties by tap index): offs[i] the i-th smallest offset as given (BPA: k - K/2,
+// already ascending), perm[i] its tap.  One CTA; a tap's position is the number of taps before it in that order.
+__global__ void __launch_bounds__(256)
+td_sort_taps_kernel(const int32_t *__restrict__ o, int K, int bpa, int32_t *__restrict__ offs, int32_t *__restrict__ perm) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int v = bpa ? k - K / 2 : __ldg(o + k);
+        int rank = k;
+        if (!bpa) {
+            rank = 0;
+            for (int j = 0; j < K; ++j) {
+                const int u = __ldg(o + j);
+                rank += (u < v) || (u == v && j < k);
+            }
+        }
+        offs[rank] = v;
+        perm[rank] = k;
+    }
+}
+
+// The B operand tiled as td_tcw_kernel reads it: block (row block rb, sorted tap i, chunk c) holds the B hi tile
+// then the B lo tile of rows rb*64 .. rb*64+63 and samples 16c .. 16c+15 (coefficient x window x phasor, each
+// sample's phasor taken directly; rows (r, re) = [v.re, -v.im], (r, im) = [v.im, v.re]; rows past n_rng zero).
+// Grid (chunks, K, row blocks), 256 threads = 64 rows x 4 groups of 4 samples.
 template <bool BPA>
 __global__ void __launch_bounds__(256)
-td_plan_kernel(const float *__restrict__ win, const float2 *__restrict__ w, const int32_t *__restrict__ o, TdParams p,
-               int K, uint4 *__restrict__ plan) {
-    __shared__ float4 tab[TP_ROWS];
-    const int k = blockIdx.x, r0 = blockIdx.y * TP_ROWS;
-    const int off = BPA ? k - K / 2 : pmod(__ldg(o + k), p.n_az);
-    if (threadIdx.x < TP_ROWS) {
-        const int r = r0 + threadIdx.x;
+td_btile_kernel(const float *__restrict__ win, const float2 *__restrict__ w, const int32_t *__restrict__ offs,
+                const int32_t *__restrict__ perm, TdParams p, int K, uint8_t *__restrict__ Bt) {
+    using namespace tcg;
+    __shared__ float4 tab[BR];
+    const int c = blockIdx.x, i = blockIdx.y, rb = blockIdx.z;
+    const int chunks = p.L / MC;
+    const int k = __ldg(perm + i);
+    const int o_n = pmod(__ldg(offs + i), p.n_az);
+    if (threadIdx.x < BR) {
+        const int r = rb * BR + threadIdx.x;
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < p.n_rng) {
-            t = tap_entry<BPA>(p, r, off);
+            t = tap_entry<BPA>(p, r, o_n);
             if (!BPA) {
-                const float2 c = __ldg(w + (size_t)r * K + k);
-                t.x = c.x;
-                t.y = c.y;
+                const float2 cw = __ldg(w + (size_t)r * K + k);
+                t.x = cw.x;
+                t.y = cw.y;
             }
         }
         tab[threadIdx.x] = t;
     }
     __syncthreads();
-    const int groups = p.L / 4;
-    for (int v = threadIdx.x; v < TP_ROWS * groups; v += blockDim.x) {
-        const int j = v % TP_ROWS, g = v / TP_ROWS;
-        const int r = r0 + j;
-        if (r >= p.n_rng) continue;
-        uint32_t hi[4], lo[4];
+    const int b_r = threadIdx.x & (BR - 1), b_c = threadIdx.x / BR;
+    uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int m = 4 * g + i;
-            const float2 val = phasor_term(tab[j], win ? __ldg(win + m) : 1.f, (float)m - p.m_ref);
-            tcg::split2(val.x, val.y, hi[i], lo[i]);
-        }
-        uint4 *q = plan + 2 * (((size_t)k * groups + g) * p.n_rng + r);
-        q[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        q[1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    for (int j = 0; j < 4; ++j) {
+        const int m = c * MC + 4 * b_c + j;
+        float2 val = make_float2(0.f, 0.f);
+        if (rb * BR + b_r < p.n_rng) val = phasor_term(tab[b_r], win ? __ldg(win + m) : 1.f, (float)m - p.m_ref);
+        uint32_t hi, lo;
+        split2(val.x, val.y, hi, lo);
+        re_hi[j] = hi ^ 0x80000000u;
+        re_lo[j] = lo ^ 0x80000000u;
+        im_hi[j] = __byte_perm(hi, 0, 0x1032);
+        im_lo[j] = __byte_perm(lo, 0, 0x1032);
     }
+    uint8_t *blk = Bt + (((size_t)rb * K + i) * chunks + c) * tcw::BTILE;
+    *reinterpret_cast<uint4 *>(blk + off(2 * b_r, 8 * b_c)) = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+    *reinterpret_cast<uint4 *>(blk + TILE + off(2 * b_r, 8 * b_c)) = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+    *reinterpret_cast<uint4 *>(blk + off(2 * b_r + 1, 8 * b_c)) = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+    *reinterpret_cast<uint4 *>(blk + TILE + off(2 * b_r + 1, 8 * b_c)) = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
 }
 
 // Per-row offsets: one CTA per (row, block of TR_BT pixels), two pixels per thread.  Samples are taken in
@@ -616,12 +891,16 @@ td_row_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
 
 // Cluster size for the tap split: the G (1 .. 8, at most K/4) whose clusters fill the co-resident cluster slots
 // in the most nearly whole number of waves (occupancy of the tensor-core kernel: its shared memory and threads).
-template <bool BPA>
-int pick_cluster_tc(int tiles, int K) {
-    static int cached_dev = -1, cached_tiles = -1, cached_K = -1, cached_G = 1;
+// Cluster size G (taps split over G CTAs, 1 <= G <= TD_MAX_CLUSTER, at least 4 taps each) that fills the GPU
+// in the most nearly whole number of waves (occupancy of the kernel: its shared memory and threads).
+int pick_cluster(const void *kernel, int threads, int smem, int tiles, int K) {
+    struct Entry { const void *kernel; int dev, tiles, K, G; };
+    static Entry cache[8] = {};
+    static int next = 0;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev == cached_dev && tiles == cached_tiles && K == cached_K) return cached_G;
+    for (const Entry &e : cache)
+        if (e.kernel == kernel && e.dev == dev && e.tiles == tiles && e.K == K) return e.G;
     int best_G = 1;
     double best = -1.0;
     for (int G = 1; G <= TD_MAX_CLUSTER; ++G) {
@@ -629,8 +908,8 @@ int pick_cluster_tc(int tiles, int K) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3(1, 1, G);
-        cfg.blockDim = dim3(tcg::THREADS);
-        cfg.dynamicSmemBytes = tcg::SMEM;
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = 1;
         attr[0].val.clusterDim.y = 1;
@@ -638,7 +917,7 @@ int pick_cluster_tc(int tiles, int K) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, td_tc_kernel<BPA>, &cfg) != cudaSuccess || clusters < 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess || clusters < 1) {
             cudaGetLastError();
             continue;
         }
@@ -649,21 +928,19 @@ int pick_cluster_tc(int tiles, int K) {
             best_G = G;
         }
     }
-    cached_dev = dev;
-    cached_tiles = tiles;
-    cached_K = K;
-    cached_G = best_G;
+    cache[next] = Entry{kernel, dev, tiles, K, best_G};
+    next = (next + 1) % 8;
     return best_G;
 }
 
 template <bool BPA>
 rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
-                       float2 *out, cudaStream_t s, const uint4 *bplan = nullptr) {
+                       float2 *out, cudaStream_t s) {
     static int done[kMaxDevices] = {};
     rosar_status st = ensure_smem((const void *)td_tc_kernel<BPA>, tcg::SMEM, done, BPA ? "bpa_time" : "sas_time");
     if (st != ROSAR_OK) return st;
     const int gx = (p.n_az + tcg::BT - 1) / tcg::BT, gy = (p.n_rng + tcg::BR - 1) / tcg::BR;
-    const int G = pick_cluster_tc<BPA>(gx * gy, K);
+    const int G = pick_cluster((const void *)td_tc_kernel<BPA>, tcg::THREADS, tcg::SMEM, gx * gy, K);
     const int k_per = (K + G - 1) / G;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -677,37 +954,80 @@ rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, con
     attr[0].val.clusterDim.z = G;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tc_kernel<BPA>, raw, win, w, o, p, K, k_per, out, bplan);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tc_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
     if (e != cudaSuccess)
         return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", BPA ? "bpa_time" : "sas_time", cudaGetErrorString(e));
     return check_launch(BPA ? "bpa_time" : "sas_time");
+}
+
+template <bool BPA>
+rosar_status launch_tcw(const float2 *raw, const uint8_t *Bt, const int32_t *offs, const TdParams &p, int K, float2 *out,
+                        cudaStream_t s) {
+    static int done[kMaxDevices] = {};
+    const char *what = BPA ? "bpa_time_planned" : "sas_time_planned";
+    rosar_status st = ensure_smem((const void *)td_tcw_kernel<BPA>, tcw::SMEM, done, what);
+    if (st != ROSAR_OK) return st;
+    const int gx = (p.n_az + tcg::BT - 1) / tcg::BT, gy = (p.n_rng + tcg::BR - 1) / tcg::BR;
+    const int G = pick_cluster((const void *)td_tcw_kernel<BPA>, tcw::THREADS, tcw::SMEM, gx * gy, K);
+    const int k_per = (K + G - 1) / G;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(gx, gy, G);
+    cfg.blockDim = dim3(tcw::THREADS);
+    cfg.dynamicSmemBytes = tcw::SMEM;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = G;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tcw_kernel<BPA>, raw, Bt, offs, p, K, k_per, out);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
+    return check_launch(what);
 }
 
 }  // namespace
 
 int time_domain_sample_multiple() { return TD_MC; }
 
-size_t time_domain_plan_bytes(int n_rng, int L, int K) { return (size_t)8 * (size_t)n_rng * (size_t)L * (size_t)K; }
+namespace {
+size_t td_tile_bytes(int n_rng, int L, int K) {
+    return (size_t)((n_rng + tcg::BR - 1) / tcg::BR) * (size_t)K * (size_t)(L / TD_MC) * (size_t)tcw::BTILE;
+}
+}  // namespace
+
+// [row blocks][sorted taps][chunks] B blocks of 16 KB, then the sorted offsets and their taps (int32 each)
+size_t time_domain_plan_bytes(int n_rng, int L, int K) {
+    return td_tile_bytes(n_rng, L, K) + (((size_t)8 * (size_t)K + 15) & ~(size_t)15);
+}
 
 rosar_status launch_time_domain_plan(const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
                                      bool bpa, void *plan, cudaStream_t s) {
     if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain plan: L=%d is not a multiple of %d", p.L, TD_MC);
-    const int gy = (p.n_rng + TP_ROWS - 1) / TP_ROWS;
-    if (gy > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain plan: n_rng=%d too large", p.n_rng);
-    dim3 grid(K, gy);
-    if (bpa) td_plan_kernel<true><<<grid, 256, 0, s>>>(win, w, o, p, K, static_cast<uint4 *>(plan));
-    else td_plan_kernel<false><<<grid, 256, 0, s>>>(win, w, o, p, K, static_cast<uint4 *>(plan));
+    const int rbs = (p.n_rng + tcg::BR - 1) / tcg::BR;
+    if (rbs > 65535 || K > 65535)
+        return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain plan: n_rng=%d or K=%d too large", p.n_rng, K);
+    uint8_t *Bt = static_cast<uint8_t *>(plan);
+    int32_t *offs = reinterpret_cast<int32_t *>(Bt + td_tile_bytes(p.n_rng, p.L, K));
+    int32_t *perm = offs + K;
+    td_sort_taps_kernel<<<1, 256, 0, s>>>(o, K, bpa ? 1 : 0, offs, perm);
+    rosar_status st = check_launch(bpa ? "bpa_time_plan" : "sas_time_plan");
+    if (st != ROSAR_OK) return st;
+    dim3 grid(p.L / TD_MC, K, rbs);
+    if (bpa) td_btile_kernel<true><<<grid, 256, 0, s>>>(win, w, offs, perm, p, K, Bt);
+    else td_btile_kernel<false><<<grid, 256, 0, s>>>(win, w, offs, perm, p, K, Bt);
     return check_launch(bpa ? "bpa_time_plan" : "sas_time_plan");
 }
 
-rosar_status launch_time_domain_planned(const float2 *raw, const int32_t *o, const TdParams &p, int K, bool bpa,
-                                        const void *plan, float2 *out, cudaStream_t s) {
+rosar_status launch_time_domain_planned(const float2 *raw, const TdParams &p, int K, bool bpa, const void *plan,
+                                        float2 *out, cudaStream_t s) {
     if (p.L % TD_MC != 0) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: L=%d is not a multiple of %d", p.L, TD_MC);
     if ((p.n_rng + tcg::BR - 1) / tcg::BR > 65535)
         return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
-    const uint4 *bp = static_cast<const uint4 *>(plan);
-    return bpa ? launch_tc<true>(raw, nullptr, nullptr, nullptr, p, K, out, s, bp)
-               : launch_tc<false>(raw, nullptr, nullptr, o, p, K, out, s, bp);
+    const uint8_t *Bt = static_cast<const uint8_t *>(plan);
+    const int32_t *offs = reinterpret_cast<const int32_t *>(Bt + td_tile_bytes(p.n_rng, p.L, K));
+    return bpa ? launch_tcw<true>(raw, Bt, offs, p, K, out, s) : launch_tcw<false>(raw, Bt, offs, p, K, out, s);
 }
 
 rosar_status launch_time_domain(const float2 *raw, const float *win, const float2 *w, const int32_t *o,

@@ -173,7 +173,8 @@ def sas_time(raw, win, w, o, radar: Radar, centred=True, out=None, stream=None):
 @dataclass(frozen=True)
 class TimeDomainPlan:
     """The precomputed B operand of the tensor-core time-domain forms (rosar_*_time_plan): a uint8 device tensor
-    of rosar_time_domain_plan_bytes(n_rng, L, K) bytes, with the shape it was made for."""
+    of rosar_time_domain_plan_bytes(n_rng, L, K) bytes (the taps' B tiles in ascending offset order and the
+    sorted offsets), with the shape it was made for."""
 
     data: torch.Tensor
     n_az: int
@@ -202,15 +203,15 @@ def sas_time_plan(win, w, o, radar: Radar, n_az, L, centred=True, stream=None):
     return TimeDomainPlan(data, n_az, L, n_rng, K)
 
 
-def sas_time_planned(raw, plan: TimeDomainPlan, o, out=None, stream=None):
-    """rosar_sas_time_planned: rosar_sas_time of raw [n_az, L] with a plan from sas_time_plan (same offsets o)."""
+def sas_time_planned(raw, plan: TimeDomainPlan, out=None, stream=None):
+    """rosar_sas_time_planned: rosar_sas_time of raw [n_az, L] with a plan from sas_time_plan (which holds the
+    offsets)."""
     lib = _lib.load()
     require(raw, torch.complex64, "raw", shape=(plan.n_az, plan.L))
-    require(o, torch.int32, "o", shape=(plan.K,))
     if out is None:
         out = torch.empty((plan.n_rng, plan.n_az), dtype=torch.complex64, device=raw.device)
     require(out, torch.complex64, "out", shape=(plan.n_rng, plan.n_az))
-    check(lib.rosar_sas_time_planned(ptr(raw), ptr(plan.data), ptr(o), plan.n_az, plan.L, plan.n_rng, plan.K, ptr(out),
+    check(lib.rosar_sas_time_planned(ptr(raw), ptr(plan.data), plan.n_az, plan.L, plan.n_rng, plan.K, ptr(out),
                                      stream_handle(stream)))
     return out
 

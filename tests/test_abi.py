@@ -237,11 +237,15 @@ def test_time_domain_plans_reject_bad_arguments(lib):
     rad = L.RadarStruct(77e9, 1e14, 1e-7, 8e-6, 0.25, 0.0)
     FAKE3 = ctypes.c_void_p(0x30000000)
     n = lib.rosar_time_domain_plan_bytes(64, 64, 16)
-    assert n == 8 * 64 * 64 * 16
+    assert n == 16384 * 1 * 16 * 4 + 8 * 16
+    assert lib.rosar_time_domain_plan_bytes(65, 32, 3) == 16384 * 2 * 3 * 2 + 32
     assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 64, 64, 16, 1, FAKE3, n - 1, None) == 1
     assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 48 + 2, 64, 16, 1, FAKE3, n, None) == 2
     assert lib.rosar_sas_time_plan(None, FAKE, FAKE2, ctypes.byref(rad), 360, 64, 64, 16, 1, ctypes.c_void_p(0x30000008),
                                    n, None) == 1                                        # plan not 16-byte aligned
-    assert lib.rosar_bpa_time_plan(None, ctypes.byref(rad), 360, 64, 64, 361, FAKE3, 8 * 64 * 64 * 361, None) == 1
-    assert lib.rosar_sas_time_planned(FAKE, FAKE3, None, 360, 64, 64, 16, FAKE2, None) == 1      # null o
+    assert lib.rosar_bpa_time_plan(None, ctypes.byref(rad), 360, 64, 64, 361, FAKE3,
+                                   lib.rosar_time_domain_plan_bytes(64, 64, 361), None) == 1   # M_ap > n_az
+    assert lib.rosar_sas_time_planned(FAKE, None, 360, 64, 64, 16, FAKE2, None) == 1            # null plan
+    assert lib.rosar_sas_time_planned(ctypes.c_void_p(0x10000008), FAKE3, 360, 64, 64, 16, FAKE2, None) == 1  # raw
+    assert lib.rosar_sas_time_planned(FAKE, FAKE3, 360, 40, 64, 16, FAKE2, None) == 2            # L % 16
     assert lib.rosar_bpa_time_planned(FAKE, FAKE3, 360, 64, 64, 60, FAKE, None) == 1            # out aliases raw

@@ -149,22 +149,45 @@ def test_sas_time_planned_matches_oracle_and_unplanned(rosar, torch, centred):
     win = dev(torch, synth.hann_window(cfg.L))
     plan = rosar.sas_time_plan(win, dev(torch, w), dev(torch, o), api_radar(rosar, cfg), cfg.n_az, cfg.L,
                                centred=centred)
-    assert plan.data.numel() == 8 * cfg.L * cfg.L * cfg.K
+    assert plan.data.numel() == 16384 * (cfg.L // 64) * cfg.K * (cfg.L // 16) + 8 * cfg.K
     ref = O.sas_time(sc.raw, synth.hann_window(cfg.L), w, o, oracle_radar(cfg), cfg.L, centred=centred)
-    got = host(rosar.sas_time_planned(dev(torch, sc.raw), plan, dev(torch, o)))
+    got = host(rosar.sas_time_planned(dev(torch, sc.raw), plan))
     assert rel_l2(got, ref) <= TOL
     unplanned = host(rosar.sas_time(dev(torch, sc.raw), win, dev(torch, w), dev(torch, o), api_radar(rosar, cfg),
                                     centred=centred))
     assert rel_l2(got, unplanned) <= TOL
     raw2 = np.roll(sc.raw, 41, axis=0)
-    got2 = host(rosar.sas_time_planned(dev(torch, raw2), plan, dev(torch, o)))
+    got2 = host(rosar.sas_time_planned(dev(torch, raw2), plan))
     assert rel_l2(got2, np.roll(ref, 41, axis=1)) <= TOL
 
 
-@pytest.mark.parametrize("n_az,L,n_rng,M_ap", [(200, 48, 45, 13), (97, 32, 1, 97), (360, 64, 64, 60)])
+@pytest.mark.parametrize("n_az,K,spread", [(1200, 16, 500), (300, 24, 900), (640, 40, 150)])
+def test_sas_time_planned_wide_unsorted_offsets(rosar, torch, n_az, K, spread):
+    """Shared offsets in no order, spread wider than one staged window of pulses (several windows per chunk),
+    with repeats, values past n_az and below -n_az (taken modulo n_az): the planned SAS against the oracle and
+    the unplanned tensor-core call."""
+    L, n_rng = 48, 70
+    o_rad, a_rad = _radar_pair(rosar, L)
+    rng = np.random.default_rng(n_az + K)
+    o = rng.integers(-spread, spread, K).astype(np.int32)
+    o[1] = o[0]                                          # a repeated offset
+    o[2] += 3 * n_az                                     # the same pulse as o[2] - 3 n_az
+    o[3] -= 2 * n_az
+    w = crand(rng, n_rng, K)
+    raw = crand(rng, n_az, L)
+    win = rng.uniform(0.1, 1.0, L).astype(np.float32)
+    plan = rosar.sas_time_plan(dev(torch, win), dev(torch, w), dev(torch, o), a_rad, n_az, L)
+    got = host(rosar.sas_time_planned(dev(torch, raw), plan))
+    assert rel_l2(got, O.sas_time(raw, win, w, o, o_rad, n_rng)) <= TOL
+    unplanned = host(rosar.sas_time(dev(torch, raw), dev(torch, win), dev(torch, w), dev(torch, o), a_rad))
+    assert rel_l2(got, unplanned) <= TOL
+
+
+@pytest.mark.parametrize("n_az,L,n_rng,M_ap", [(200, 48, 45, 13), (97, 32, 1, 97), (360, 64, 64, 60),
+                                               (1000, 32, 64, 400)])
 def test_bpa_time_planned_ragged(rosar, torch, n_az, L, n_rng, M_ap):
     """Planned time-domain BPA on ragged tiles (rows and azimuth off the tile, L a multiple of 16 but not a
-    power of two, one row, the whole ring) against the oracle."""
+    power of two, one row, the whole ring, a tap range wider than one staged window) against the oracle."""
     o_rad, a_rad = _radar_pair(rosar, L)
     rng = np.random.default_rng(n_az + 3 * L)
     raw = crand(rng, n_az, L)
@@ -186,7 +209,7 @@ def test_time_domain_planned_full_size_sampled_pixels(rosar, torch):
     rows = np.concatenate([rng.integers(1, cfg.L, 20), [cfg.L - 1]])
     thetas = np.concatenate([rng.integers(0, cfg.n_az, 20), [cfg.n_az - 1]])
     plan = rosar.sas_time_plan(dev(torch, win), dev(torch, w), dev(torch, o), api_radar(rosar, cfg), cfg.n_az, cfg.L)
-    sas = host(rosar.sas_time_planned(dev(torch, sc.raw), plan, dev(torch, o)))
+    sas = host(rosar.sas_time_planned(dev(torch, sc.raw), plan))
     assert rel_l2(sas[rows, thetas], O.sas_time_pixels(sc.raw, win, w, o, o_rad, cfg.n_az, rows, thetas)) <= TOL
     bplan = rosar.bpa_time_plan(dev(torch, win), api_radar(rosar, cfg), cfg.n_az, cfg.L, cfg.L, cfg.M_ap)
     bpa = host(rosar.bpa_time_planned(dev(torch, sc.raw), bplan))
