@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--indoor-steps", type=int, default=2000, help="timed scans of the indoor section")
     ap.add_argument("--per-scan", action="store_true",
                     help="indoor section: one rosar_image_fft call per scan instead of the pipelined call")
+    ap.add_argument("--kernel-cases", type=int, default=0, metavar="N",
+                    help="profiling mode: run every profiled call twice on small cases (the indoor scan, a 16-scan "
+                         "stack, the first N scans of the batched workload), print the launch order and exit")
     return ap.parse_args()
 
 
@@ -1241,9 +1244,67 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def kernel_cases(args):
+    """Every call whose kernels the profile summaries cover, on small cases, run twice in a fixed order (the first
+    pass warms up; an ncu capture skips it).  No timing: the launch list and counters come from the profiler."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2309_08038_gb300 as rosar
+    rosar.load()
+    device = torch.device("cuda", 0)
+    cfg, sc, raw_stack, raws, w, o, win = indoor_inputs(torch, device, 0)
+    radar = api_radar(rosar, cfg)
+    S = rosar.range_compress(raws[0], win)
+    dphi = torch.from_numpy(sc.dphi.astype(np.float32)).to(device)
+    dr = torch.from_numpy(sc.dr.astype(np.float32)).to(device)
+    dl = torch.from_numpy(synth.migration_offsets(cfg, o.cpu().numpy())).to(device)
+    H = rosar.azimuth_plan(w, o, cfg.n_az)
+    mplan = rosar.azimuth_plan_migrating(w, o, dl, cfg.n_az)
+    stack = rosar.range_compress(raw_stack, win)                     # [16][L][n_az]
+    g = torch.randn_like(stack)
+    eps = torch.randn((raw_stack.shape[0], cfg.n_az), device=device) * 0.3
+    P = rosar.phasors(eps)
+    X, G = torch.empty_like(stack), torch.empty_like(stack)
+    ref = torch.randn_like(stack)
+    splan = rosar.sas_time_plan(win, w, o, radar, cfg.n_az, cfg.L)
+    bplan = rosar.bpa_time_plan(win, radar, cfg.n_az, cfg.L, cfg.L, cfg.M_ap)
+    wl = BatchedWorkload(torch, rosar, device, args.kernel_cases)
+    b = rosar.Batch(wl.scans, rosar.batch.Tuning())
+    ws2 = torch.empty((2, cfg.L, cfg.n_az), dtype=torch.complex64, device=device)
+    calls = [
+        ("range_compress_kernel", lambda: rosar.range_compress(raws[0], win, out=S)),
+        ("sparse_azimuth_kernel", lambda: rosar.sparse_azimuth(S, w, o)),
+        ("azimuth_fft_fixed_kernel", lambda: rosar.sparse_azimuth_fft(S, H)),
+        ("bpa_kernel<nominal>", lambda: rosar.bpa(S, radar, cfg.L, cfg.M_ap)),
+        ("bpa_kernel<supplied errors>", lambda: rosar.bpa(S, radar, cfg.L, cfg.M_ap, dphi=dphi, dr=dr)),
+        ("migrating spectrum + combine", lambda: rosar.sparse_azimuth_migrating_fft(S, mplan)),
+        ("diff forward filter", lambda: rosar.sparse_azimuth_fft_scans_ex(stack, H, P=P, spectrum=X)),
+        ("loss partial + final", lambda: rosar.image_l2_loss(stack, ref)),
+        ("loss grad", lambda: rosar.image_l2_loss_grad(stack, ref, torch.ones((), device=device))),
+        ("diff adjoint filter", lambda: rosar.sparse_azimuth_fft_scans_ex(g, H, adjoint=True, spectrum=G)),
+        ("weight grad (accumulate + taps)", lambda: rosar.azimuth_weight_grad_spectra(G, X, o, cfg.K)),
+        ("phase grad", lambda: rosar.phase_grad_phasor(stack, P, g)),
+        ("image_stage_kernel (3 scans)", lambda: rosar.image_fft_scans(raw_stack[:3], win, H, workspace=ws2)),
+        (f"batch_kernel ({args.kernel_cases} scans)", lambda: b.launch()),
+        ("td_tc_kernel<BPA>", lambda: rosar.bpa_time(raws[0], win, radar, cfg.L, cfg.M_ap)),
+        ("td_tc_kernel<SAS>", lambda: rosar.sas_time(raws[0], win, w, o, radar)),
+        ("td_tcw_kernel<BPA>", lambda: rosar.bpa_time_planned(raws[0], bplan)),
+        ("td_tcw_kernel<SAS>", lambda: rosar.sas_time_planned(raws[0], splan)),
+    ]
+    for _ in range(2):
+        for _, c in calls:
+            c()
+        torch.cuda.synchronize()
+    b.status()                                    # raises if a dependency wait gave up
+    print(json.dumps({"kernel_cases": [name for name, _ in calls], "batch_scans": args.kernel_cases}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernel_cases:
+        kernel_cases(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

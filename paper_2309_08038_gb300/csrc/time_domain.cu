@@ -483,8 +483,8 @@ using namespace tcg;
 constexpr int NS = 3;                              // B stage buffers
 constexpr int WMAX = 248;                          // window rows: 128 pixels + the segment's offset span
 constexpr int SPAN = WMAX - BT;                    // largest offset span of one segment
-constexpr int ALBO = WMAX * 16 + 64;               // K-adjacent core matrices of the window (+64 B: the four
-                                                   // 16-byte groups of a window store fall in distinct banks)
+constexpr int ALBO = WMAX * 16 + 32;               // K-adjacent core matrices of the window (+32 B: a half-warp's
+                                                   // 8-byte window stores, 2 rows x 4 groups, cover 32 banks once)
 constexpr int ASBO = 128;                          // 8-row groups of the window
 constexpr int APLANE = 4 * ALBO;                   // hi plane, then lo plane
 constexpr int WSLOT = 2 * APLANE;
