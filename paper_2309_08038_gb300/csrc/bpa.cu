@@ -20,8 +20,8 @@
 // and the pixel loop is two gathers, an interpolation and a complex MAC.
 //
 // With supplied errors the fine phase exp(-j*2*pi*(2*f_mid/c)*delta) of every (pixel, pulse) is taken as
-// sin/cos of an angle first reduced exactly by whole turns to [-pi, pi] (delta spans tens of cycles) and then
-// evaluated by the hardware sine and cosine (about 1e-6 absolute error there), instead of the accurate
+// sin/cos of the phase in turns first reduced exactly by whole turns to [-1/2, 1/2] (delta spans tens of cycles)
+// and then evaluated by the hardware sine and cosine (about 1e-6 absolute error there), instead of the accurate
 // sincospif's software range reduction and polynomials: the per-sample work is issue-bound FP32 and SFU.
 // The interpolation mode is a template parameter.
 //
@@ -33,10 +33,12 @@ namespace rosar {
 namespace {
 
 constexpr int BPA_THREADS = 256;
-constexpr int BPA_DC = 512;   // aperture offsets staged per chunk
 constexpr int BPA_WR = 6;     // range rows of the staged S window
-constexpr int BPA_WC = BPA_THREADS + BPA_DC;   // columns (pulses) of the window
-constexpr int BPA_SMEM = BPA_WR * BPA_WC * 8;  // 36 KB
+// aperture offsets staged per chunk: 512 with nominal geometry; 256 with supplied errors, whose per-pulse table
+// makes a CTA's shared memory the occupancy limit (256: 6 CTAs per SM instead of 3)
+template <bool NOMINAL> constexpr int bpa_dc() { return NOMINAL ? 512 : 256; }
+template <bool NOMINAL> constexpr int bpa_wc() { return BPA_THREADS + bpa_dc<NOMINAL>(); }   // window columns (pulses)
+template <bool NOMINAL> constexpr int bpa_smem() { return BPA_WR * bpa_wc<NOMINAL>() * 8; }
 
 __device__ __forceinline__ float2 read_bin(const float2 *__restrict__ S, int l, int L, size_t col, int n_az) {
     return (l >= 0 && l < L) ? __ldg(S + (size_t)l * n_az + col) : make_float2(0.f, 0.f);
@@ -47,12 +49,12 @@ __device__ __forceinline__ float2 read_bin(const float2 *__restrict__ S, int l, 
 // (one bin of margin each side) and the pulses th0 + dc .. th0 + dc + BPA_WC are staged in shared memory once, and
 // every (pixel, pulse) sample whose two bins fall in the window reads it there (others, e.g. under large supplied
 // position errors, read S through L2 as before).
-// exp(-j*pi*x) for |x| up to 2^22: x reduced by whole turns (x - 2*rint(x/2), exact) to [-1, 1], then the
-// hardware sine and cosine of pi times the remainder.
-__device__ __forceinline__ float2 expmjpi_fast(float x) {
-    const float xr = fmaf(-2.f, rintf(0.5f * x), x);
+// exp(-j*2*pi*q) for |q| up to 2^22 turns: q reduced by whole turns (q - rint(q), exact) to [-1/2, 1/2], then
+// the hardware sine and cosine of 2*pi times the remainder.
+__device__ __forceinline__ float2 expmj2pi_turns(float q) {
+    const float r = q - rintf(q);
     float sn, cs;
-    __sincosf(3.14159265358979f * xr, &sn, &cs);
+    __sincosf(6.28318530717959f * r, &sn, &cs);
     return make_float2(cs, -sn);
 }
 
@@ -60,6 +62,7 @@ template <bool NOMINAL, bool LINEAR>
 __global__ void __launch_bounds__(BPA_THREADS)
 bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ dphi, const float *__restrict__ dr,
            int L, int n_az, int M_ap, float2 *__restrict__ out) {
+    constexpr int BPA_DC = bpa_dc<NOMINAL>(), BPA_WC = bpa_wc<NOMINAL>();
     extern __shared__ float2 wsm[];                           // [BPA_WR][BPA_WC]
     __shared__ float4 dtab[BPA_DC];                           // NOMINAL: (x, a.re, a.im, -); else (sin, cos, x_nominal, -)
     // per pulse, with this CTA's row folded in: (cos(eps/2), sin(eps/2), dr*(r_n + r0 - 2R), 4*R*r_n), and
@@ -87,8 +90,11 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
 
     float2 acc = make_float2(0.f, 0.f);
     const int d_beg = -(M_ap / 2), d_end = M_ap - M_ap / 2;
-    for (int dc = d_beg; dc < d_end; dc += BPA_DC) {
-        const int nd = min(BPA_DC, d_end - dc);
+    // chunks of equal size (at most BPA_DC offsets): M = 600 with BPA_DC = 256 gives 3 chunks of 200
+    const int n_chunks = (M_ap + BPA_DC - 1) / BPA_DC;
+    const int step = (M_ap + n_chunks - 1) / n_chunks;
+    for (int dc = d_beg; dc < d_end; dc += step) {
+        const int nd = min(step, d_end - dc);
         __syncthreads();
         float xlo = 1e30f, xhi = -1e30f;
         for (int i = threadIdx.x; i < nd; i += BPA_THREADS) {
@@ -160,8 +166,6 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
         }
         __syncthreads();
         if (th < n_az) {
-            int n = th + dc;
-            n = n < 0 ? n + n_az : (n >= n_az ? n - n_az : n);
 #pragma unroll 4
             for (int i = 0; i < nd; ++i) {
                 const float4 t = dtab[i];
@@ -186,9 +190,8 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                         delta = 0.f;
                         alpha = 1.f;
                     }
-                    const float2 ph = expmjpi_fast(2.f * p.two_f_over_c * delta);
                     x = fmaf(delta, p.inv_dR, rf);
-                    a = make_float2(alpha * ph.x, alpha * ph.y);
+                    a = cscale(expmj2pi_turns(p.two_f_over_c * delta), alpha);
                 }
                 const int col = threadIdx.x + i;
                 float2 sv;
@@ -200,17 +203,18 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                     if (l0 >= wlo && l0 + 1 < wtop) {
                         s0 = wsm[(l0 - wlo) * BPA_WC + col];
                         s1 = wsm[(l0 + 1 - wlo) * BPA_WC + col];
-                    } else {
+                    } else {                  // off the staged window: pulse (th + d) mod n_az through L2
+                        const int n = pmod(th + dc + i, n_az);
                         s0 = read_bin(S, l0, L, n, n_az);
                         s1 = read_bin(S, l0 + 1, L, n, n_az);
                     }
                     sv = caxpy(f, csub(s1, s0), s0);
                 } else {
                     const int l0 = (int)floorf(x + 0.5f);
-                    sv = (l0 >= wlo && l0 < wtop) ? wsm[(l0 - wlo) * BPA_WC + col] : read_bin(S, l0, L, n, n_az);
+                    sv = (l0 >= wlo && l0 < wtop) ? wsm[(l0 - wlo) * BPA_WC + col]
+                                                  : read_bin(S, l0, L, pmod(th + dc + i, n_az), n_az);
                 }
                 cmac(acc, a, sv);
-                if (++n == n_az) n = 0;
             }
         }
     }
@@ -228,13 +232,14 @@ rosar_status launch_bpa(const float2 *S, const BpaParams &p, const float *dphi, 
     const int v = (nominal ? 0 : 2) + (interp ? 1 : 0);
     static const void *const ks[4] = {(const void *)bpa_kernel<true, false>, (const void *)bpa_kernel<true, true>,
                                       (const void *)bpa_kernel<false, false>, (const void *)bpa_kernel<false, true>};
-    rosar_status st = ensure_smem(ks[v], BPA_SMEM, done[v], "bpa");
+    const int smem = nominal ? bpa_smem<true>() : bpa_smem<false>();
+    rosar_status st = ensure_smem(ks[v], smem, done[v], "bpa");
     if (st != ROSAR_OK) return st;
     switch (v) {
-        case 0: bpa_kernel<true, false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
-        case 1: bpa_kernel<true, true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
-        case 2: bpa_kernel<false, false><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
-        default: bpa_kernel<false, true><<<grid, BPA_THREADS, BPA_SMEM, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        case 0: bpa_kernel<true, false><<<grid, BPA_THREADS, smem, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        case 1: bpa_kernel<true, true><<<grid, BPA_THREADS, smem, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        case 2: bpa_kernel<false, false><<<grid, BPA_THREADS, smem, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
+        default: bpa_kernel<false, true><<<grid, BPA_THREADS, smem, s>>>(S, p, dphi, dr, L, n_az, M_ap, out); break;
     }
     return check_launch("bpa");
 }
