@@ -489,6 +489,7 @@ constexpr int ASBO = 128;                          // 8-row groups of the window
 constexpr int APLANE = 4 * ALBO;                   // hi plane, then lo plane
 constexpr int WSLOT = 2 * APLANE;
 constexpr int BTILE = 2 * TILE;                    // planned B block (hi, lo)
+constexpr int WROUNDS = (WMAX + PRODUCERS / 8 - 1) / (PRODUCERS / 8);   // window rows per producer thread
 constexpr int THREADS = PRODUCERS + 64;            // warps 0-7 windows / fold / epilogue, 8 MMA issuer, 9 B copies
 constexpr int SMEM = NS * BTILE + 2 * WSLOT + 128; // + mbarriers and the TMEM slot
 static_assert(SMEM <= 232448 / 2 - 1024, "two CTAs per SM");
@@ -573,16 +574,28 @@ td_tcw_kernel(const float2 *__restrict__ X, const uint8_t *__restrict__ Bt, cons
             const int p0 = pmod(th0 + pmod(__ldg(offs + ka), n_az), n_az);
             uint8_t *ws = wbase + slot * WSLOT + a_dst;
             const float2 *col = X + c * MC + 2 * a_j;
-#pragma unroll 2
-            for (int i = a_r; i < W; i += PRODUCERS / 8) {
-                int pulse = p0 + i;
-                if (pulse >= n_az) pulse %= n_az;
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(col + (size_t)pulse * L));
-                uint2 hi, lo;
-                split2(v.x, v.y, hi.x, lo.x);
-                split2(v.z, v.w, hi.y, lo.y);
-                *reinterpret_cast<uint2 *>(ws + 16 * i) = hi;
-                *reinterpret_cast<uint2 *>(ws + APLANE + 16 * i) = lo;
+            // all of this thread's rows (at most WROUNDS) loaded before any is converted: one memory round trip
+            float4 v[WROUNDS];
+#pragma unroll
+            for (int j = 0; j < WROUNDS; ++j) {
+                const int i = a_r + j * (PRODUCERS / 8);
+                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < W) {
+                    int pulse = p0 + i;
+                    if (pulse >= n_az) pulse %= n_az;
+                    v[j] = __ldg(reinterpret_cast<const float4 *>(col + (size_t)pulse * L));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < WROUNDS; ++j) {
+                const int i = a_r + j * (PRODUCERS / 8);
+                if (i < W) {
+                    uint2 hi, lo;
+                    split2(v[j].x, v[j].y, hi.x, lo.x);
+                    split2(v[j].z, v[j].w, hi.y, lo.y);
+                    *reinterpret_cast<uint2 *>(ws + 16 * i) = hi;
+                    *reinterpret_cast<uint2 *>(ws + APLANE + 16 * i) = lo;
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
