@@ -492,6 +492,7 @@ constexpr int BTILE = 2 * TILE;                    // planned B block (hi, lo)
 constexpr int WROUNDS = (WMAX + PRODUCERS / 8 - 1) / (PRODUCERS / 8);   // window rows per producer thread
 constexpr int THREADS = PRODUCERS + 64;            // warps 0-7 windows / fold / epilogue, 8 MMA issuer, 9 B copies
 constexpr int SMEM = NS * BTILE + 2 * WSLOT + 128; // + mbarriers and the TMEM slot
+static_assert((2 * NS + 6) * 8 + 4 <= 128, "barriers and the TMEM slot fit their area");
 static_assert(SMEM <= 232448 / 2 - 1024, "two CTAs per SM");
 static_assert(BT * NN * 4 <= NS * BTILE + 2 * WSLOT, "the cluster reduction parks a tile in the stage buffers");
 
@@ -704,6 +705,370 @@ td_tcw_kernel(const float2 *__restrict__ X, const uint8_t *__restrict__ Bt, cons
         // the copies of the last (up to NS) issued stages may still be in flight if a wait gave up: their
         // completion is the only arrival their phase needs (bounded waits)
         for (int s2 = max(0, s - NS); s2 < s; ++s2) wait_bar(&full[s2 % NS], (uint32_t)((s2 / NS) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    const int th = 32 * q + lane;
+    float v[64];
+    if (producer) {
+        if (ok && stages > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ld16(x_ta + 16 * c, v + 16 * c);
+                if (have_y) {
+                    float yv[16];
+                    ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[16 * c + j] += yv[j];
+                }
+            }
+        } else {
+            const float f = ok ? 0.f : __int_as_float(0x7fc00000);   // no taps: zero; a wait that gave up: NaN
+#pragma unroll
+            for (int j = 0; j < 64; ++j) v[j] = f;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+
+    const int G = gridDim.z;
+    bool writer = producer;
+    if (G > 1) {                              // partial tiles parked in the stage buffers, rank 0 adds in rank order
+        float *red = reinterpret_cast<float *>(smem);            // [128 columns][128 pixels] = 64 KB
+        cg::cluster_group cluster = cg::this_cluster();
+        if (producer) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) red[(64 * h + j) * BT + th] = v[j];
+        }
+        cluster.sync();
+        if (producer && cluster.block_rank() == 0) {
+            for (int rk = 1; rk < G; ++rk) {
+                const float *rem = cluster.map_shared_rank(red, rk);
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] += rem[(64 * h + j) * BT + th];
+            }
+        }
+        cluster.sync();
+        writer = producer && cluster.block_rank() == 0;
+    }
+    const int tcol = th0 + th;
+    if (writer && tcol < n_az) {
+#pragma unroll
+        for (int j = 0; j < 64; j += 2) {
+            const int r = r0 + (64 * h + j) / 2;
+            if (r < p.n_rng) out[(size_t)r * n_az + tcol] = make_float2(v[j], v[j + 1]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ generated-B tensor-core form (sliding A window) --
+// td_tcw_kernel's pipeline without a plan: the producer warps generate each stage's B tile (coefficient x window
+// x fast-time phasor of 64 rows x 16 samples, each sample's phasor taken directly: the phase in half-turns
+// reduced exactly by whole turns, then the hardware sine and cosine) into a 3-deep ring, and stage the raw-pulse
+// windows as in td_tcw_kernel.  A tenth warp sorts the CTA's taps by offset once and fills, two tap groups ahead,
+// the per-(row, tap) table (coefficient, two-way phase, fast-time phase in FP64 -> float hi/lo) that the B tiles
+// are made from.  Taps run in groups of at most TG sorted taps within SPAN pulses; stage order = group, chunk,
+// tap.  The window of group g and chunk c + 1 is staged after the producers have generated the first NS stages
+// of chunk c (by then the MMAs of the window before have finished, so its slot is free).
+namespace tcgn {
+using namespace tcg;
+constexpr int NS = 3;                              // B stage buffers
+constexpr int TG = 8;                              // taps per group (table entries per row)
+constexpr int WMAX = 176;                          // window rows
+constexpr int SPAN = WMAX - BT;
+constexpr int ALBO = WMAX * 16 + 32;               // as td_tcw_kernel (+32 B: conflict-free window stores)
+constexpr int ASBO = 128;
+constexpr int APLANE = 4 * ALBO;
+constexpr int WSLOT = 2 * APLANE;
+constexpr int WROUNDS = (WMAX + PRODUCERS / 8 - 1) / (PRODUCERS / 8);
+constexpr int BSTAGE = 2 * TILE;                   // B hi, B lo
+constexpr int TAPS_MAX = 512;                      // taps per CTA (the sorted list in shared memory)
+constexpr int TABLE = TG * BR * 16;                // one table slot: [TG][64 rows] float4
+constexpr int OFF_WIN = NS * BSTAGE;
+constexpr int OFF_TAB = OFF_WIN + 2 * WSLOT;
+constexpr int OFF_SORT = OFF_TAB + 2 * TABLE;
+constexpr int OFF_BAR = OFF_SORT + 2 * TAPS_MAX * 4;
+constexpr int N_BARS = 2 * NS + 2 * 4 + 2;         // full, empty, wfull, wempty, tfull, tempty, fold, acc
+constexpr int SMEM = OFF_BAR + 256;                // the barriers, then the TMEM address slot
+static_assert(N_BARS * 8 + 4 <= 256, "barriers and the TMEM slot fit their area");
+constexpr int THREADS = PRODUCERS + 64;            // warps 0-7 producers, 8 MMA issuer, 9 sort and tables
+static_assert(SMEM <= 233472 / 2 - 1024, "two CTAs per SM");
+static_assert(BT * NN * 4 <= OFF_TAB, "the cluster reduction parks a tile in the stage and window buffers");
+__device__ __forceinline__ uint64_t descA(uint32_t a) {
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(ALBO >> 4) << 16) | ((uint64_t)(ASBO >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+}  // namespace tcgn
+
+// c * win * exp(-j*pi*phi*x) as phasor_term, with the hardware sine and cosine of the reduced argument (|arg| <=
+// about 1 half-turn; absolute error about 1e-6, below the bf16 split's 2^-16 relative)
+__device__ __forceinline__ float2 phasor_term_fast(float4 t, float wm, float x) {
+    const float prod = t.z * x;
+    const float err = fmaf(t.z, x, -prod);
+    const float red = prod - 2.f * rintf(0.5f * prod);
+    const float arg = red + fmaf(t.w, x, err);
+    float sn, cs;
+    __sincosf(3.14159265358979f * arg, &sn, &cs);
+    const float2 c = make_float2(t.x * wm, t.y * wm);
+    return cmul(c, make_float2(cs, -sn));
+}
+
+template <bool BPA>
+__global__ void __launch_bounds__(tcgn::THREADS, 2)
+td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const float2 *__restrict__ w,
+              const int32_t *__restrict__ o, TdParams p, int K, int k_per, float2 *__restrict__ out) {
+    using namespace tcgn;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *bstage = smem;                                          // [NS][B hi, B lo]
+    uint8_t *wbase = smem + OFF_WIN;                                 // [2][hi, lo][4 groups][ALBO]
+    float4 *tab = reinterpret_cast<float4 *>(smem + OFF_TAB);        // [2][TG][BR]
+    int *soff = reinterpret_cast<int *>(smem + OFF_SORT);            // sorted offsets of this CTA's taps
+    int *stap = soff + TAPS_MAX;                                     // and their taps
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+    uint64_t *full = bars, *empty = bars + NS, *wfull = bars + 2 * NS, *wempty = wfull + 2, *tfull = wempty + 2,
+             *tempty = tfull + 2, *fold_bar = tempty + 2, *acc_bar = fold_bar + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_bar + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp < PRODUCERS / 32;
+    const int th0 = blockIdx.x * BT, r0 = blockIdx.y * BR;
+    const int n_az = p.n_az, L = p.L;
+    const int chunks = L / MC;
+    const int k_lo = blockIdx.z * k_per;
+    const int nk = max(0, min(K, k_lo + k_per) - k_lo);
+    const int stages = nk * chunks;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[i])), "r"(PRODUCERS / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&empty[i])), "r"(1));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&wfull[i])), "r"(PRODUCERS / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&wempty[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&tfull[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&tempty[i])), "r"(PRODUCERS / 32));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(fold_bar)), "r"(PRODUCERS / 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(acc_bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == PRODUCERS / 32 + 1) {         // the CTA's taps in ascending offset order (ties by tap)
+        for (int i = lane; i < nk; i += 32) {
+            const int k = k_lo + i;
+            const int v = BPA ? k - K / 2 : __ldg(o + k);
+            int rank = i;
+            if (!BPA) {
+                rank = 0;
+                for (int j = 0; j < nk; ++j) {
+                    const int u = __ldg(o + k_lo + j);
+                    rank += (u < v) || (u == v && j < i);
+                }
+            }
+            soff[rank] = v;
+            stap[rank] = k;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    const uint32_t x_ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
+    const uint32_t y_ta = x_ta + (uint32_t)NN;
+    bool have_y = false;
+    bool ok = true;
+
+    // group of sorted taps starting at ga: at most TG taps within SPAN of soff[ga]
+    auto group_end = [&](int ga) {
+        const long long base = soff[ga];
+        int gb = ga + 1;
+        while (gb < nk && gb - ga < TG && (long long)soff[gb] - base <= SPAN) ++gb;
+        return gb;
+    };
+
+    if (producer) {
+        const int a_j = tid & 7, a_r = tid >> 3;
+        const int a_dst = (a_j >> 1) * ALBO + (a_j & 1) * 8;
+        auto produce = [&](int wi, int c, int ga, int gb) {           // window wi = (group [ga, gb), chunk c)
+            const int slot = wi & 1;
+            if (wi >= 2 && ok) ok = wait_bar(&wempty[slot], (uint32_t)(((wi >> 1) - 1) & 1));
+            const int W = (int)((long long)soff[gb - 1] - soff[ga]) + BT;
+            const int p0 = pmod(th0 + pmod(soff[ga], n_az), n_az);
+            uint8_t *ws = wbase + slot * WSLOT + a_dst;
+            const float2 *col = X + c * MC + 2 * a_j;
+            float4 v[WROUNDS];
+#pragma unroll
+            for (int j = 0; j < WROUNDS; ++j) {
+                const int i = a_r + j * (PRODUCERS / 8);
+                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < W) {
+                    int pulse = p0 + i;
+                    if (pulse >= n_az) pulse %= n_az;
+                    v[j] = __ldg(reinterpret_cast<const float4 *>(col + (size_t)pulse * L));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < WROUNDS; ++j) {
+                const int i = a_r + j * (PRODUCERS / 8);
+                if (i < W) {
+                    uint2 hi, lo;
+                    split2(v[j].x, v[j].y, hi.x, lo.x);
+                    split2(v[j].z, v[j].w, hi.y, lo.y);
+                    *reinterpret_cast<uint2 *>(ws + 16 * i) = hi;
+                    *reinterpret_cast<uint2 *>(ws + APLANE + 16 * i) = lo;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&wfull[slot])) : "memory");
+        };
+        auto fold = [&]() {
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float xv[16], yv[16];
+                ld16(x_ta + 16 * c, xv);
+                if (have_y) {
+                    ld16(y_ta + 16 * c, yv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) xv[j] += yv[j];
+                }
+                st16(y_ta + 16 * c, xv);
+            }
+            have_y = true;
+        };
+        // B: thread = (row b_r = 8 warp + (lane & 7), samples 4 (lane >> 3) ..); lanes with b_r & 4 write the im
+        // row first, so each 8-lane phase of a 16-byte store hits 8 distinct rows
+        const int b_r = 8 * warp + (lane & 7), b_c = lane >> 3;
+        const bool b_swap = (b_r & 4) != 0;
+        const int b_re = off(2 * b_r, 8 * b_c), b_im = off(2 * b_r + 1, 8 * b_c);
+        const int b_first = b_swap ? b_im : b_re, b_second = b_swap ? b_re : b_im;
+        if (stages > 0) {
+            int s = 0, wi = 0, g = 0;
+            int ga = 0, gb = group_end(0);
+            produce(0, 0, ga, gb);
+            for (; ga < nk; ga = gb, gb = gb < nk ? group_end(gb) : gb, ++g) {
+                const int tslot = g & 1;
+                if (ok) ok = wait_bar(&tfull[tslot], (uint32_t)((g >> 1) & 1));
+                const float4 *tg = tab + tslot * (TG * BR);
+                for (int c = 0; c < chunks; ++c, ++wi) {
+                    const int n_w = gb - ga;
+                    const int j_next = min(NS, n_w) - 1;                 // stage after which window wi + 1 is staged
+                    for (int kk = 0; kk < n_w; ++kk, ++s) {
+                        const int b = s % NS;
+                        if (s >= NS && ok) ok = wait_bar(&empty[b], (uint32_t)(((s / NS) - 1) & 1));
+                        uint8_t *st = bstage + b * BSTAGE;
+                        const float4 t4 = tg[kk * BR + b_r];
+                        const int mb = c * MC + 4 * b_c;
+                        uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float wm = win ? __ldg(win + mb + i) : 1.f;
+                            const float2 v = phasor_term_fast(t4, wm, (float)(mb + i) - p.m_ref);
+                            uint32_t hi, lo;
+                            split2(v.x, v.y, hi, lo);
+                            re_hi[i] = hi ^ 0x80000000u;
+                            re_lo[i] = lo ^ 0x80000000u;
+                            im_hi[i] = __byte_perm(hi, 0, 0x1032);
+                            im_lo[i] = __byte_perm(lo, 0, 0x1032);
+                        }
+                        const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+                        const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+                        const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+                        const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+                        *reinterpret_cast<uint4 *>(st + b_first) = b_swap ? ih : rh;
+                        *reinterpret_cast<uint4 *>(st + TILE + b_first) = b_swap ? il : rl;
+                        *reinterpret_cast<uint4 *>(st + b_second) = b_swap ? rh : ih;
+                        *reinterpret_cast<uint4 *>(st + TILE + b_second) = b_swap ? rl : il;
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[b])) : "memory");
+                        if (kk == j_next) {                                // stage the next window
+                            if (c + 1 < chunks) produce(wi + 1, c + 1, ga, gb);
+                            else if (gb < nk) produce(wi + 1, 0, gb, group_end(gb));
+                        }
+                        if ((s + 1) % PERIOD == 0 && s + 1 < stages) {     // period end: fold X into Y
+                            if (ok) ok = wait_bar(acc_bar, (uint32_t)((s / PERIOD) & 1));
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            if (ok) fold();
+                            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0)
+                                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(fold_bar)) : "memory");
+                        }
+                    }
+                }
+                __syncwarp();                                              // the group's table is no longer read
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&tempty[tslot])) : "memory");
+            }
+            if (ok) ok = wait_bar(acc_bar, (uint32_t)(((stages - 1) / PERIOD) & 1));
+        }
+    } else if (warp == PRODUCERS / 32) {
+        if (lane == 0) {                      // the MMA issuer
+            int s = 0, wi = 0;
+            for (int ga = 0, gb = 0; ga < nk && ok; ga = gb) {
+                gb = group_end(ga);
+                for (int c = 0; c < chunks && ok; ++c, ++wi) {
+                    const int slot = wi & 1;
+                    ok = wait_bar(&wfull[slot], (uint32_t)((wi >> 1) & 1));
+                    if (!ok) break;
+                    const long long base = soff[ga];
+                    const uint32_t wa = saddr(wbase + slot * WSLOT);
+                    for (int k = ga; k < gb; ++k, ++s) {
+                        const int b = s % NS;
+                        ok = wait_bar(&full[b], (uint32_t)((s / NS) & 1));
+                        if (ok && s % PERIOD == 0 && s > 0) ok = wait_bar(fold_bar, (uint32_t)((s / PERIOD - 1) & 1));
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a_hi = wa + (uint32_t)(((long long)soff[k] - base) * 16), a_lo = a_hi + APLANE;
+                        const uint32_t b_hi = saddr(bstage + b * BSTAGE), b_lo = b_hi + TILE;
+#pragma unroll
+                        for (int ks = 0; ks < KR / 16; ++ks) {
+                            const uint32_t ka2 = ks * 2 * ALBO, kb2 = ks * 2 * LBO;
+                            mma(tmem, descA(a_hi + ka2), desc(b_hi + kb2), (s % PERIOD != 0 || ks > 0) ? 1u : 0u);
+                            mma(tmem, descA(a_hi + ka2), desc(b_lo + kb2), 1u);
+                            mma(tmem, descA(a_lo + ka2), desc(b_hi + kb2), 1u);
+                        }
+                        commit(&empty[b]);
+                        if ((s + 1) % PERIOD == 0 || s + 1 == stages) commit(acc_bar);
+                    }
+                    if (!ok) break;
+                    if (c + 1 < chunks || gb < nk) commit(&wempty[slot]);
+                }
+            }
+        }
+    } else {                                  // warp 9: the per-(row, tap) tables, two groups ahead
+        int g = 0;
+        for (int ga = 0, gb = 0; ga < nk && ok; ga = gb, ++g) {
+            gb = group_end(ga);
+            const int slot = g & 1;
+            if (g >= 2) ok = wait_bar(&tempty[slot], (uint32_t)(((g >> 1) - 1) & 1));
+            if (!ok) break;
+            float4 *tg = tab + slot * (TG * BR);
+            for (int e = lane; e < (gb - ga) * BR; e += 32) {
+                const int kk = e / BR, j = e - kk * BR;
+                const int r = r0 + j;
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < p.n_rng) {
+                    t = tap_entry<BPA>(p, r, pmod(soff[ga + kk], n_az));
+                    if (!BPA) {
+                        const float2 cw = __ldg(w + (size_t)r * K + stap[ga + kk]);
+                        t.x = cw.x;
+                        t.y = cw.y;
+                    }
+                }
+                tg[kk * BR + j] = t;
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&tfull[slot])) : "memory");
+        }
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -974,6 +1339,36 @@ rosar_status launch_tc(const float2 *raw, const float *win, const float2 *w, con
 }
 
 template <bool BPA>
+rosar_status launch_tcg(const float2 *raw, const float *win, const float2 *w, const int32_t *o, const TdParams &p, int K,
+                        float2 *out, cudaStream_t s, bool *used) {
+    *used = false;
+    static int done[kMaxDevices] = {};
+    const char *what = BPA ? "bpa_time" : "sas_time";
+    rosar_status st = ensure_smem((const void *)td_tcg_kernel<BPA>, tcgn::SMEM, done, what);
+    if (st != ROSAR_OK) return st;
+    const int gx = (p.n_az + tcg::BT - 1) / tcg::BT, gy = (p.n_rng + tcg::BR - 1) / tcg::BR;
+    const int G = pick_cluster((const void *)td_tcg_kernel<BPA>, tcgn::THREADS, tcgn::SMEM, gx * gy, K);
+    const int k_per = (K + G - 1) / G;
+    if (k_per > tcgn::TAPS_MAX) return ROSAR_OK;             // the caller runs td_tc_kernel instead
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(gx, gy, G);
+    cfg.blockDim = dim3(tcgn::THREADS);
+    cfg.dynamicSmemBytes = tcgn::SMEM;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = G;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, td_tcg_kernel<BPA>, raw, win, w, o, p, K, k_per, out);
+    if (e != cudaSuccess) return set_error(ROSAR_ERR_CUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
+    *used = true;
+    return check_launch(what);
+}
+
+template <bool BPA>
 rosar_status launch_tcw(const float2 *raw, const uint8_t *Bt, const int32_t *offs, const TdParams &p, int K, float2 *out,
                         cudaStream_t s) {
     static int done[kMaxDevices] = {};
@@ -1049,6 +1444,10 @@ rosar_status launch_time_domain(const float2 *raw, const float *win, const float
     if (bpa || o_row_stride == 0) {
         if ((p.n_rng + tcg::BR - 1) / tcg::BR > 65535)
             return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
+        bool used = false;
+        rosar_status st = bpa ? launch_tcg<true>(raw, win, w, o, p, K, out, s, &used)
+                              : launch_tcg<false>(raw, win, w, o, p, K, out, s, &used);
+        if (st != ROSAR_OK || used) return st;
         return bpa ? launch_tc<true>(raw, win, w, o, p, K, out, s) : launch_tc<false>(raw, win, w, o, p, K, out, s);
     }
     if (p.n_rng > 65535) return set_error(ROSAR_ERR_UNSUPPORTED, "time-domain: n_rng=%d too large", p.n_rng);
