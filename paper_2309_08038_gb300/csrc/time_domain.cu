@@ -801,17 +801,16 @@ __device__ __forceinline__ uint64_t descA(uint32_t a) {
 }
 }  // namespace tcgn
 
-// c * win * exp(-j*pi*phi*x) as phasor_term, with the hardware sine and cosine of the reduced argument (|arg| <=
-// about 1 half-turn; absolute error about 1e-6, below the bf16 split's 2^-16 relative)
-__device__ __forceinline__ float2 phasor_term_fast(float4 t, float wm, float x) {
-    const float prod = t.z * x;
-    const float err = fmaf(t.z, x, -prod);
+// exp(-j*pi*phi*x) for phi = hi + lo, reduced as in phasor_term, with the hardware sine and cosine of the reduced
+// argument (|arg| <= about 1 half-turn; absolute error about 1e-6, below the bf16 split's 2^-16 relative)
+__device__ __forceinline__ float2 phasor_unit_fast(float hi, float lo, float x) {
+    const float prod = hi * x;
+    const float err = fmaf(hi, x, -prod);
     const float red = prod - 2.f * rintf(0.5f * prod);
-    const float arg = red + fmaf(t.w, x, err);
+    const float arg = red + fmaf(lo, x, err);
     float sn, cs;
     __sincosf(3.14159265358979f * arg, &sn, &cs);
-    const float2 c = make_float2(t.x * wm, t.y * wm);
-    return cmul(c, make_float2(cs, -sn));
+    return make_float2(cs, -sn);
 }
 
 template <bool BPA>
@@ -949,6 +948,7 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
         const bool b_swap = (b_r & 4) != 0;
         const int b_re = off(2 * b_r, 8 * b_c), b_im = off(2 * b_r + 1, 8 * b_c);
         const int b_first = b_swap ? b_im : b_re, b_second = b_swap ? b_re : b_im;
+        const uint32_t sel_first = b_swap ? 0x1032u : 0x7654u, sel_second = b_swap ? 0x7654u : 0x1032u;
         if (stages > 0) {
             int s = 0, wi = 0, g = 0;
             int ga = 0, gb = group_end(0);
@@ -966,26 +966,31 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
                         uint8_t *st = bstage + b * BSTAGE;
                         const float4 t4 = tg[kk * BR + b_r];
                         const int mb = c * MC + 4 * b_c;
-                        uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+                        // the phasor at the thread's first sample taken directly, the next three by the one-sample
+                        // step (three products: about 3e-7 more error)
+                        float2 e = phasor_unit_fast(t4.z, t4.w, (float)mb - p.m_ref);
+                        const float2 step = phasor_unit_fast(t4.z, t4.w, 1.f);
+                        uint32_t f_hi[4], f_lo[4], s_hi[4], s_lo[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const float wm = win ? __ldg(win + mb + i) : 1.f;
-                            const float2 v = phasor_term_fast(t4, wm, (float)(mb + i) - p.m_ref);
+                            const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
+                            if (i < 3) e = cmul(e, step);
                             uint32_t hi, lo;
                             split2(v.x, v.y, hi, lo);
-                            re_hi[i] = hi ^ 0x80000000u;
-                            re_lo[i] = lo ^ 0x80000000u;
-                            im_hi[i] = __byte_perm(hi, 0, 0x1032);
-                            im_lo[i] = __byte_perm(lo, 0, 0x1032);
+                            // row (re) = the pair with the high half's sign flipped (bytes 4-7 of the selector
+                            // pair), row (im) = the pair with its halves swapped (bytes 2, 3, 0, 1): the first
+                            // store of a lane takes the im row where b_swap
+                            const uint32_t hs = hi ^ 0x80000000u, ls = lo ^ 0x80000000u;
+                            f_hi[i] = __byte_perm(hi, hs, sel_first);
+                            f_lo[i] = __byte_perm(lo, ls, sel_first);
+                            s_hi[i] = __byte_perm(hi, hs, sel_second);
+                            s_lo[i] = __byte_perm(lo, ls, sel_second);
                         }
-                        const uint4 rh = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
-                        const uint4 rl = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
-                        const uint4 ih = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
-                        const uint4 il = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
-                        *reinterpret_cast<uint4 *>(st + b_first) = b_swap ? ih : rh;
-                        *reinterpret_cast<uint4 *>(st + TILE + b_first) = b_swap ? il : rl;
-                        *reinterpret_cast<uint4 *>(st + b_second) = b_swap ? rh : ih;
-                        *reinterpret_cast<uint4 *>(st + TILE + b_second) = b_swap ? rl : il;
+                        *reinterpret_cast<uint4 *>(st + b_first) = make_uint4(f_hi[0], f_hi[1], f_hi[2], f_hi[3]);
+                        *reinterpret_cast<uint4 *>(st + TILE + b_first) = make_uint4(f_lo[0], f_lo[1], f_lo[2], f_lo[3]);
+                        *reinterpret_cast<uint4 *>(st + b_second) = make_uint4(s_hi[0], s_hi[1], s_hi[2], s_hi[3]);
+                        *reinterpret_cast<uint4 *>(st + TILE + b_second) = make_uint4(s_lo[0], s_lo[1], s_lo[2], s_lo[3]);
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
                         if (lane == 0)
