@@ -193,10 +193,12 @@ ROSAR_API rosar_status rosar_image_fft_host(const rosar_c32 *raw_host, const flo
  * tau_k = 2*rho_k/c with rho_k the nominal slant range (Eq. (2)) from the phase
  * centre at radius r0 and angle 2*pi*(theta + o_k)/n_az to the pixel at
  * distance R_r = r0 + r*dR and angle 2*pi*theta/n_az, dR = c/(2*K*t_s*L).
- * Cost O(K*L) per pixel (the FFT+ forms cost O(K)); FP32 arithmetic with the
- * per-(r, k) slant range and two-way phase in FP64.  win may be NULL (all
- * ones, the paper's unwindowed sums).  Requires L a multiple of 16 and raw
- * 16-byte aligned.  out must not overlap raw.
+ * Cost O(K*L) per pixel (the FFT+ forms cost O(K)); the per-(r, k) slant range
+ * and two-way phase in FP64, the sums on the tensor cores with each operand
+ * split into bf16 hi + lo parts (three products per term, FP32 accumulation:
+ * within a few 1e-5 of FP32), taps summed in ascending offset order.  win may
+ * be NULL (all ones, the paper's unwindowed sums).  Requires L a multiple of 16
+ * and raw 16-byte aligned.  out must not overlap raw.
  * ------------------------------------------------------------------------ */
 
 /*
