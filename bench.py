@@ -1000,27 +1000,33 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
         pp = float(cfg.M_ap) * px                              # pixel-pulses of one BPA image
         res["compare"] = {
             "fft_bpa_px_s": world * px / (t_bj + t_k1), "fft_bpa_nominal_px_s": world * px / (t_bn + t_k1),
-            "bpa_kernel<1>": bpa_entry(t_bj, pp, BPA_FLOPS_ERR, 4, fp32_peak, sfu_peak),
-            "bpa_kernel<0>": bpa_entry(t_bn, pp, BPA_FLOPS_NOM, 0, fp32_peak, sfu_peak),
-            "bpa_note": "bpa_kernel<1> = supplied rotation errors, <0> = nominal geometry; algorithmic work per "
+            "bpa_kernel<0,1> (supplied errors)": dict(bpa_entry(t_bj, pp, BPA_FLOPS_ERR, 4, fp32_peak, sfu_peak),
+                                  traffic=recorded_traffic("bpa_kernel<0,1>", "indoor", source_hash("bpa.cu"))),
+            "bpa_kernel<1,1> (nominal)": dict(bpa_entry(t_bn, pp, BPA_FLOPS_NOM, 0, fp32_peak, sfu_peak),
+                                  traffic=recorded_traffic("bpa_kernel<1,1>", "indoor", source_hash("bpa.cu"))),
+            "bpa_note": "bpa_kernel<NOMINAL, LINEAR>, linear interpolation; algorithmic work per "
                         "pixel-pulse: nominal 12 flop (linear interpolation 4, complex MAC 8), supplied errors "
                         "34 flop and 4 SFU ops (rsqrt, reciprocal, sine, cosine); peaks derived at the measured "
                         "SM clock: FP32 152 SMs x 128 lanes x 2 flop, SFU 152 SMs x 16 ops per clock; both "
                         "variants are bound by instruction issue (ncu: 76-86 % issue active)",
             "bpa_time_px_s": world * px / t_bt, "sas_time_px_s": world * px / t_st,
-            "td_tc_kernel<BPA>": {"us_per_launch": t_bt * 1e6, "tflops": f_bt / t_bt / 1e12,
+            "td_tcg_kernel<BPA>": {"us_per_launch": t_bt * 1e6, "tflops": f_bt / t_bt / 1e12,
                                   "tensor_frac": 3 * f_bt / t_bt / 1e12 / bf16_peak,
-                                  "traffic": recorded_traffic("td_tc_kernel<1>", "indoor", source_hash("time_domain.cu"))},
-            "td_tc_kernel<SAS>": {"us_per_launch": t_st * 1e6, "tflops": f_st / t_st / 1e12,
+                                  "traffic": recorded_traffic("td_tcg_kernel<1>", "indoor", source_hash("time_domain.cu"))},
+            "td_tcg_kernel<SAS>": {"us_per_launch": t_st * 1e6, "tflops": f_st / t_st / 1e12,
                                   "tensor_frac": 3 * f_st / t_st / 1e12 / bf16_peak,
-                                  "traffic": recorded_traffic("td_tc_kernel<0>", "indoor", source_hash("time_domain.cu"))},
+                                  "traffic": recorded_traffic("td_tcg_kernel<0>", "indoor", source_hash("time_domain.cu"))},
             "planned": {
                 "td_tcw_kernel<SAS>": {"us_per_launch": t_stp * 1e6, "tflops": f_st / t_stp / 1e12,
                                        "tensor_frac": 3 * f_st / t_stp / 1e12 / bf16_peak,
-                                       "plan_us_once": t_splan * 1e6, "plan_MB": plan_mb[0]},
+                                       "plan_us_once": t_splan * 1e6, "plan_MB": plan_mb[0],
+                                       "traffic": recorded_traffic("td_tcw_kernel<0>", "indoor",
+                                                                   source_hash("time_domain.cu"))},
                 "td_tcw_kernel<BPA>": {"us_per_launch": t_btp * 1e6, "tflops": f_bt / t_btp / 1e12,
                                        "tensor_frac": 3 * f_bt / t_btp / 1e12 / bf16_peak,
-                                       "plan_us_once": t_bplan * 1e6, "plan_MB": plan_mb[1]},
+                                       "plan_us_once": t_bplan * 1e6, "plan_MB": plan_mb[1],
+                                       "traffic": recorded_traffic("td_tcw_kernel<1>", "indoor",
+                                                                   source_hash("time_domain.cu"))},
                 "note": "B operand (coefficient x window x phasor, bf16 hi/lo, tiled as the tensor cores read it) "
                         "computed once per weight design; per scan the kernel stages one window of raw pulses per "
                         "16-sample chunk shared by all taps within 120 pulses, and streams the B tiles by bulk copy; "
@@ -1030,10 +1036,11 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
                                          "SAS (B built per image + planned kernel)": (t_splan + t_stp) * 1e3,
                                          "FFT+BPA": (t_bn + t_k1) * 1e3,
                                          "FFT+SAS": ms / steps, "FFT+SAS (per-pulse peak bins)": t_migf_img * 1e3},
-            "note": "FFT+BPA = range compression + back-projection over M=600 pulses (bpa_kernel<1>: supplied "
-                    "rotation errors, per pixel-pulse geometry; <0>: nominal); BPA / SAS = time-domain forms "
-                    "(Eq. (14); Algorithm 2 with W_SA) on the tensor cores, tensor_frac of the measured sustained "
-                    "bf16 peak executed (3 split-bf16 products per term); FFT+SAS = the timed indoor path"}
+            "note": "FFT+BPA = range compression + back-projection over M=600 pulses (nominal geometry; the "
+                    "supplied-error variant is timed beside it); BPA / SAS = time-domain forms (Eq. (14); "
+                    "Algorithm 2 with W_SA) on the tensor cores, unplanned (B generated in the kernel) and with B "
+                    "built per image by the plan kernels then the planned kernel; tensor_frac of the measured "
+                    "sustained bf16 peak executed (3 split-bf16 products per term); FFT+SAS = the timed indoor path"}
         res["highres"] = highres_bench(torch, rosar, device, world, hbm)
     return res, indoor_img, (cfg, sc, w, o, win)
 
@@ -1318,8 +1325,8 @@ def kernel_cases(args):
         ("phase grad", lambda: rosar.phase_grad_phasor(stack, P, g)),
         ("image_stage_kernel (3 scans)", lambda: rosar.image_fft_scans(raw_stack[:3], win, H, workspace=ws2)),
         (f"batch_kernel ({args.kernel_cases} scans)", lambda: b.launch()),
-        ("td_tc_kernel<BPA>", lambda: rosar.bpa_time(raws[0], win, radar, cfg.L, cfg.M_ap)),
-        ("td_tc_kernel<SAS>", lambda: rosar.sas_time(raws[0], win, w, o, radar)),
+        ("td_tcg_kernel<BPA> (unplanned call)", lambda: rosar.bpa_time(raws[0], win, radar, cfg.L, cfg.M_ap)),
+        ("td_tcg_kernel<SAS> (unplanned call)", lambda: rosar.sas_time(raws[0], win, w, o, radar)),
         ("td_tcw_kernel<BPA>", lambda: rosar.bpa_time_planned(raws[0], bplan)),
         ("td_tcw_kernel<SAS>", lambda: rosar.sas_time_planned(raws[0], splan)),
     ]
