@@ -65,6 +65,23 @@ def test_bpa_time_ragged(rosar, torch, n_az, L, n_rng, M_ap):
     assert rel_l2(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("n_az,M_ap", [(4200, 4200), (3000, 2600)])
+def test_bpa_time_wide_aperture(rosar, torch, n_az, M_ap):
+    """Apertures of thousands of pulses: 2600 taps run as ~40 groups of sorted taps per CTA in the window
+    kernel, 4200 taps exceed the taps one CTA of it holds (more than 512 per cluster rank) and take the per-tap
+    kernel; sampled pixels against the oracle."""
+    L, n_rng = 16, 3
+    o_rad, a_rad = _radar_pair(rosar, L)
+    rng = np.random.default_rng(n_az + M_ap)
+    raw = crand(rng, n_az, L)
+    win = rng.uniform(0.1, 1.0, L).astype(np.float32)
+    got = host(rosar.bpa_time(dev(torch, raw), dev(torch, win), a_rad, n_rng, M_ap))
+    rows = np.array([0, 1, 2, 1, 2, 2])
+    thetas = np.array([0, 1, n_az // 2, n_az - 1, 777, 2999])
+    ref = O.bpa_time_pixels(raw, win, o_rad, n_az, M_ap, rows, thetas)
+    assert rel_l2(got[rows, thetas], ref) <= TOL
+
+
 @pytest.mark.parametrize("per_row", [False, True])
 def test_sas_time_ragged_and_wrapping_offsets(rosar, torch, per_row):
     """Offsets anywhere in int32 range (taken modulo n_az, including beyond +-n_az), ragged tiles,
