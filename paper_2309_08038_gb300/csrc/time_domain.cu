@@ -17,11 +17,14 @@
 //
 // With offsets shared by all rows the filter is an implicit complex GEMM over the index (k, m):
 //   out[theta][r] = sum_(k,m) A[theta][(k,m)] * B[(k,m)][r],  A = raw[theta + o_k][m],  B = c*win*phasor,
-// run on the tensor cores (td_tc_kernel below): 128 azimuth pixels x 64 rows per CTA, per stage (one tap,
-// 16 samples) an A tile of raw samples and a B tile of generated coefficients in shared memory, tcgen05 MMAs
-// into a tensor-memory accumulator.  Per-row offsets (Algorithm 2 with a support per range bin) use a row
-// kernel on the CUDA cores: one row per CTA, the row's phasors staged in shared memory by sample chunk,
-// pulses read through L1/L2.
+// run on the tensor cores: 128 azimuth pixels x 64 rows per CTA, per stage (one tap, 16 samples) an A tile of
+// raw samples and a B tile of coefficients in shared memory, tcgen05 MMAs into a tensor-memory accumulator.
+// Three kernels share that tiling: td_tcg_kernel (the unplanned calls: B generated per stage, A from a window
+// of raw pulses shared by the taps of a group), td_tcw_kernel (the planned calls: B precomputed once per weight
+// design and bulk-copied) and td_tc_kernel (A and B both built per stage; taken when a CTA's taps exceed the
+// others' sorted-tap list).  Per-row offsets (Algorithm 2 with a support per range bin) use a row kernel on the
+// CUDA cores: one row per CTA, the row's phasors staged in shared memory by sample chunk, pulses read through
+// L1/L2.
 //
 // 8 flops per (pixel, tap, sample).
 
@@ -90,7 +93,8 @@ __device__ __forceinline__ float2 phasor_term(float4 t, float wm, float x) {
 // x fast-time phasor, split) into shared memory in the canonical no-swizzle K-major layout (8 x 16-byte core
 // matrices; K-adjacent ones 128 B apart, 8-row groups 512 B apart), double-buffered; one thread issues the 2 K
 // steps x 3 MMAs (M = 128, N = 128, K = 16) and commits them to the stage buffer's mbarrier, which the
-// producers wait on before refilling that buffer.  Taps split across a cluster as in td_tile_kernel.
+// producers wait on before refilling that buffer.  Taps split across a cluster of CTAs whose partial tiles
+// rank 0 adds in rank order.
 namespace tcg {
 constexpr int PRODUCERS = 256;               // warps 0-7 stage the operands and read the accumulator
 constexpr int THREADS = PRODUCERS + 32;      // warp 8 issues the MMAs
