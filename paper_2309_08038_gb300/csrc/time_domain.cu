@@ -31,6 +31,7 @@
 #include <cooperative_groups.h>
 
 #include <cmath>
+#include <mutex>
 
 #include <cuda_bf16.h>
 
@@ -1284,10 +1285,14 @@ int pick_cluster(const void *kernel, int threads, int smem, int tiles, int K) {
     struct Entry { const void *kernel; int dev, tiles, K, G; };
     static Entry cache[8] = {};
     static int next = 0;
+    static std::mutex mu;                     // host threads may launch concurrently
     int dev = 0;
     cudaGetDevice(&dev);
-    for (const Entry &e : cache)
-        if (e.kernel == kernel && e.dev == dev && e.tiles == tiles && e.K == K) return e.G;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : cache)
+            if (e.kernel == kernel && e.dev == dev && e.tiles == tiles && e.K == K) return e.G;
+    }
     int best_G = 1;
     double best = -1.0;
     for (int G = 1; G <= TD_MAX_CLUSTER; ++G) {
@@ -1315,8 +1320,11 @@ int pick_cluster(const void *kernel, int threads, int smem, int tiles, int K) {
             best_G = G;
         }
     }
-    cache[next] = Entry{kernel, dev, tiles, K, best_G};
-    next = (next + 1) % 8;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[next] = Entry{kernel, dev, tiles, K, best_G};
+        next = (next + 1) % 8;
+    }
     return best_G;
 }
 
