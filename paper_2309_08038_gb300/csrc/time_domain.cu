@@ -768,12 +768,12 @@ td_tcw_kernel(const float2 *__restrict__ X, const uint8_t *__restrict__ Bt, cons
 }
 
 // ------------------------------------------------------------ generated-B tensor-core form (sliding A window) --
-// td_tcw_kernel's pipeline without a plan: the producer warps generate each stage's B tile (coefficient x window
-// x fast-time phasor of 64 rows x 16 samples, each sample's phasor taken directly: the phase in half-turns
-// reduced exactly by whole turns, then the hardware sine and cosine) into a 3-deep ring, and stage the raw-pulse
-// windows as in td_tcw_kernel.  A tenth warp sorts the CTA's taps by offset once and fills, two tap groups ahead,
-// the per-(row, tap) table (coefficient, two-way phase, fast-time phase in FP64 -> float hi/lo) that the B tiles
-// are made from.  Taps run in groups of at most TG sorted taps within SPAN pulses; stage order = group, chunk,
+// td_tcw_kernel's pipeline without a plan: the producer warps generate each stage's B tile (coefficient x fast-
+// time phasor of 64 rows x 16 samples: the phase in half-turns reduced exactly by whole turns, then the hardware
+// sine and cosine) into a 3-deep ring, and stage the raw-pulse windows as in td_tcw_kernel with the fast-time
+// window applied to A as it is staged (it depends on the sample only).  A tenth warp sorts the CTA's taps by
+// offset once and fills, two tap groups ahead, the per-(row, tap) table (coefficient, two-way phase, fast-time
+// phase in FP64 -> float hi/lo) that the B tiles are made from.  Taps run in groups of at most TG sorted taps within SPAN pulses; stage order = group, chunk,
 // tap.  The window of group g and chunk c + 1 is staged after the producers have generated the first NS stages
 // of chunk c (by then the MMAs of the window before have finished, so its slot is free).
 namespace tcgn {
@@ -907,6 +907,9 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
             const int p0 = pmod(th0 + pmod(soff[ga], n_az), n_az);
             uint8_t *ws = wbase + slot * WSLOT + a_dst;
             const float2 *col = X + c * MC + 2 * a_j;
+            // the fast-time window multiplies A here, once per staged sample, instead of every B entry
+            const float w0 = win ? __ldg(win + c * MC + 2 * a_j) : 1.f;
+            const float w1 = win ? __ldg(win + c * MC + 2 * a_j + 1) : 1.f;
             float4 v[WROUNDS];
 #pragma unroll
             for (int j = 0; j < WROUNDS; ++j) {
@@ -923,8 +926,8 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
                 const int i = a_r + j * (PRODUCERS / 8);
                 if (i < W) {
                     uint2 hi, lo;
-                    split2(v[j].x, v[j].y, hi.x, lo.x);
-                    split2(v[j].z, v[j].w, hi.y, lo.y);
+                    split2(v[j].x * w0, v[j].y * w0, hi.x, lo.x);
+                    split2(v[j].z * w1, v[j].w * w1, hi.y, lo.y);
                     *reinterpret_cast<uint2 *>(ws + 16 * i) = hi;
                     *reinterpret_cast<uint2 *>(ws + APLANE + 16 * i) = lo;
                 }
@@ -976,10 +979,10 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
                         float2 e = phasor_unit_fast(t4.z, t4.w, (float)mb - p.m_ref);
                         const float2 step = phasor_unit_fast(t4.z, t4.w, 1.f);
                         uint32_t f_hi[4], f_lo[4], s_hi[4], s_lo[4];
+                        const float2 cc = make_float2(t4.x, t4.y);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float wm = win ? __ldg(win + mb + i) : 1.f;
-                            const float2 v = cmul(make_float2(t4.x * wm, t4.y * wm), e);
+                            const float2 v = cmul(cc, e);
                             if (i < 3) e = cmul(e, step);
                             uint32_t hi, lo;
                             split2(v.x, v.y, hi, lo);
