@@ -974,16 +974,14 @@ td_tcg_kernel(const float2 *__restrict__ X, const float *__restrict__ win, const
                         uint8_t *st = bstage + b * BSTAGE;
                         const float4 t4 = tg[kk * BR + b_r];
                         const int mb = c * MC + 4 * b_c;
-                        // the phasor at the thread's first sample taken directly, the next three by the one-sample
-                        // step (three products: about 3e-7 more error)
-                        float2 e = phasor_unit_fast(t4.z, t4.w, (float)mb - p.m_ref);
+                        // coefficient x phasor at the thread's first sample (phasor taken directly), the next three
+                        // by the one-sample step (three products: about 3e-7 more error)
+                        float2 v = cmul(make_float2(t4.x, t4.y), phasor_unit_fast(t4.z, t4.w, (float)mb - p.m_ref));
                         const float2 step = phasor_unit_fast(t4.z, t4.w, 1.f);
                         uint32_t f_hi[4], f_lo[4], s_hi[4], s_lo[4];
-                        const float2 cc = make_float2(t4.x, t4.y);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float2 v = cmul(cc, e);
-                            if (i < 3) e = cmul(e, step);
+                            if (i > 0) v = cmul(v, step);
                             uint32_t hi, lo;
                             split2(v.x, v.y, hi, lo);
                             // row (re) = the pair with the high half's sign flipped (bytes 4-7 of the selector
