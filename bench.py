@@ -449,6 +449,16 @@ def quality_report(gpu_npz, tmp):
         rep["indoor"] = {"rel_l2": _rel_l2(img, ref), "peak_gpu": _peak(img), "peak_oracle": _peak(ref),
                          "peak_equal": _peak(img) == _peak(ref), "peak_margin": _peak_margin(ref),
                          "entropy_gpu": O.image_entropy(img), "entropy_oracle": O.image_entropy(ref)}
+    # the paper's methods on the same indoor scan: image entropy of each (Eq. (45)); the paper's tables order
+    # them BPA < FFT+BPA < SAS < FFT+SAS (reported here, not a gate)
+    methods = {"BPA (time domain)": "img_bpa_time", "FFT+BPA": "img_fft_bpa",
+               "FFT+BPA (supplied rotation errors)": "img_fft_bpa_errors", "SAS (time domain)": "img_sas_time",
+               "FFT+SAS": "indoor"}
+    if all(k in g.files for k in methods.values()):
+        ent = {name: O.image_entropy(g[key]) for name, key in methods.items()}
+        rep["indoor_entropy_by_method"] = ent
+        rep["paper_entropy_order_holds"] = bool(ent["BPA (time domain)"] < ent["FFT+BPA"] < ent["SAS (time domain)"]
+                                                < ent["FFT+SAS"])
     # batched workload: sampled rows of the headline launch's images
     rows_rep = []
     for key in sorted(k for k in g.files if k.startswith("batch_rows_")):
@@ -967,6 +977,12 @@ def indoor_section(torch, rosar, args, device, rank, world, stream, peaks, peak_
                              1, stream, world, device)
         ms_st, _ = time_loop(torch, lambda i: rosar.sas_time(raws[i % N_BUF], win, w, o, radar, out=bo), 20, 2,
                              stream, world, device)
+        if rank == 0:      # the paper's methods on the first scan, for the quality report's entropy comparison
+            res["_method_images"] = {
+                "img_fft_bpa_errors": rosar.bpa(S_bufs[0], radar, cfg.L, cfg.M_ap, dphi=dphi, dr=dr).cpu().numpy(),
+                "img_fft_bpa": rosar.bpa(S_bufs[0], radar, cfg.L, cfg.M_ap).cpu().numpy(),
+                "img_bpa_time": rosar.bpa_time(raws[0], win, radar, cfg.L, cfg.M_ap).cpu().numpy(),
+                "img_sas_time": rosar.sas_time(raws[0], win, w, o, radar).cpu().numpy()}
         # planned forms: the B operand (coefficient x window x phasor) computed once per weight design; a plan
         # build is timed on its second call (the first loads the kernels and allocates the plan's memory)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1225,6 +1241,8 @@ def run_ours(args):
     gpu_q["tiny"] = tiny_image(torch, rosar, device)
     if indoor_img is not None and rank == 0:
         gpu_q["indoor"] = indoor_img
+    if indoor is not None:
+        gpu_q.update(indoor.pop("_method_images", {}))
 
     # ---- differentiable form
     diff = None

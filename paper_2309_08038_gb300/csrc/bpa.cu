@@ -180,16 +180,13 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                     const float s2 = sh * sh;
                     const float num = fmaf(pp.w, s2, pp.z);                  // R_n^2 - rho^2
                     const float Rn2 = fmaf(rho, rho, num);
-                    float delta, alpha;
-                    if (Rn2 > 0.f) {
-                        const float inv = rsqrtf(Rn2);
-                        const float Rn = Rn2 * inv;
-                        delta = __fdividef(num, Rn + rho);
-                        alpha = fmaxf(0.f, fmaf(-2.f * R, s2, pal[threadIdx.x + i]) * inv);
-                    } else {
-                        delta = 0.f;
-                        alpha = 1.f;
-                    }
+                    // branch-free: R_n = 0 (the facing pulse of row 0, or a supplied position on the pixel) gives
+                    // delta = num / rho = -rho exactly, or 0 when rho = 0 too, and alpha = 1 by the select
+                    const float inv = rsqrtf(fmaxf(Rn2, 1e-30f));
+                    const float Rn = Rn2 * inv;
+                    const float delta = __fdividef(num, fmaxf(Rn + rho, 1e-30f));
+                    const float a0 = fmaxf(0.f, fmaf(-2.f * R, s2, pal[threadIdx.x + i]) * inv);
+                    const float alpha = Rn2 > 0.f ? a0 : 1.f;
                     x = fmaf(delta, p.inv_dR, rf);
                     a = cscale(expmj2pi_turns(p.two_f_over_c * delta), alpha);
                 }
