@@ -76,30 +76,18 @@ __device__ __forceinline__ void run_range(const ScanDev &sc, int n0, char *sm, b
     fft::range_tile<L, 4096 / L>(sc.raw, sc.win, sc.n_az, true, sc.S, n0, reinterpret_cast<float2 *>(sm), build,
                                  sc.vec_store != 0);
 }
+// Range lengths outside 128..1024 out of line, like fft_row_runtime below: they are rare, and inlined their
+// register needs cost the common paths spills.
+template <int L>
+__device__ __noinline__ void run_range_rare(const ScanDev &sc, int n0, char *sm, bool build) {
+    run_range<L>(sc, n0, sm, build);
+}
 
-// One range row of a scan through the frequency-domain azimuth filter (same arithmetic as
-// rosar_sparse_azimuth_fft).  S was written by this kernel's range tiles: read through L2 (ld.cg).  The row
-// lengths with a compile-time plan run the fused filter (first and last passes on global memory, H read from
-// global in the fused middle step); the others load the row, eight loads in flight per thread, and run the
-// run-time plan.
-__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem, bool discard) {
+// The rows without a compile-time plan (run-time radices), kept out of line: inlined, their register needs
+// made the whole kernel spill.
+__device__ __noinline__ void fft_row_runtime(const ScanDev &sc, const float2 *Srow, size_t row, float2 *x,
+                                             const float2 *tc, const float2 *tf) {
     const int N = sc.n_az;
-    float2 *x = reinterpret_cast<float2 *>(smem);
-    float2 *tw = x + rowfft::padded_len(N);
-    const float2 *tc, *tf;
-    rowfft::build_twiddles(N, false, tw, &tc, &tf);
-    const size_t row = (size_t)r * N;
-    const float2 *Srow = sc.S + row;
-    if (sc.fixed) {
-        __syncthreads();
-        switch (sc.fixed) {                   // the run-time plan's radices, constant strides
-            case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
-            case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
-            default: rowfft::row_filter_fused<7200, BT_THREADS, false, 8, 4, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
-        }
-        __syncthreads();
-        return;
-    }
     for (int n0 = threadIdx.x; n0 < N; n0 += 8 * BT_THREADS) {
         float2 v[8];
 #pragma unroll
@@ -126,6 +114,32 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
         sc.out[row + n] = make_float2(y.x, -y.y);
     }
     __syncthreads();
+}
+
+// One range row of a scan through the frequency-domain azimuth filter (same arithmetic as
+// rosar_sparse_azimuth_fft).  S was written by this kernel's range tiles: read through L2 (ld.cg).  The row
+// lengths with a compile-time plan run the fused filter (first and last passes on global memory, H read from
+// global in the fused middle step); the others load the row, eight loads in flight per thread, and run the
+// run-time plan.
+__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem, bool discard) {
+    const int N = sc.n_az;
+    float2 *x = reinterpret_cast<float2 *>(smem);
+    float2 *tw = x + rowfft::padded_len(N);
+    const float2 *tc, *tf;
+    rowfft::build_twiddles(N, false, tw, &tc, &tf);
+    const size_t row = (size_t)r * N;
+    const float2 *Srow = sc.S + row;
+    if (sc.fixed) {
+        __syncthreads();
+        switch (sc.fixed) {                   // the run-time plan's radices, constant strides
+            case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
+            case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
+            default: rowfft::row_filter_fused<7200, BT_THREADS, false, 8, 4, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
+        }
+        __syncthreads();
+        return;
+    }
+    fft_row_runtime(sc, Srow, row, x, tc, tf);
 }
 
 __device__ __forceinline__ int find_segment(const Segment *__restrict__ segs, int n_segs, int t) {
@@ -170,14 +184,14 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
             const bool build = tab_L != sc.L;
             const int n0 = local * sc.P;
             switch (sc.L) {
-                case 16: run_range<16>(sc, n0, sm, build); break;
-                case 32: run_range<32>(sc, n0, sm, build); break;
-                case 64: run_range<64>(sc, n0, sm, build); break;
+                case 16: run_range_rare<16>(sc, n0, sm, build); break;
+                case 32: run_range_rare<32>(sc, n0, sm, build); break;
+                case 64: run_range_rare<64>(sc, n0, sm, build); break;
                 case 128: run_range<128>(sc, n0, sm, build); break;
                 case 256: run_range<256>(sc, n0, sm, build); break;
                 case 512: run_range<512>(sc, n0, sm, build); break;
                 case 1024: run_range<1024>(sc, n0, sm, build); break;
-                default: run_range<2048>(sc, n0, sm, build); break;
+                default: run_range_rare<2048>(sc, n0, sm, build); break;
             }
             tab_L = sc.L;
             __threadfence();       // this thread's S stores are visible device-wide ...
