@@ -121,12 +121,14 @@ __device__ __noinline__ void fft_row_runtime(const ScanDev &sc, const float2 *Sr
 // lengths with a compile-time plan run the fused filter (first and last passes on global memory, H read from
 // global in the fused middle step); the others load the row, eight loads in flight per thread, and run the
 // run-time plan.
-__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem, bool discard) {
+// build_tw = false: the previous tile of this CTA was a row of the same length and left its twiddle table in
+// place (the rows write only their buffer in front of it).
+__device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *smem, bool discard, bool build_tw) {
     const int N = sc.n_az;
     float2 *x = reinterpret_cast<float2 *>(smem);
     float2 *tw = x + rowfft::padded_len(N);
-    const float2 *tc, *tf;
-    rowfft::build_twiddles(N, false, tw, &tc, &tf);
+    const float2 *tc = tw + 64, *tf = tw;           // the layout build_twiddles(N, false, ...) writes
+    if (build_tw) rowfft::build_twiddles(N, false, tw, &tc, &tf);
     const size_t row = (size_t)r * N;
     const float2 *Srow = sc.S + row;
     if (sc.fixed) {
@@ -161,6 +163,7 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
     int *head = counters + CNT_HEAD, *err = counters + CNT_ERR, *done = counters + CNT_DONE;
     const bool discard = (flags & ROSAR_BATCH_DISCARD_S) != 0;
     int tab_L = 0;   // L of the twiddle table left in shared memory by the previous range tile
+    int tab_N = 0;   // n_az of the row twiddle table left by the previous azimuth FFT tile
 
     // a CTA holds two tickets: the tile it runs and the next one, taken when the current tile starts (the
     // smallest unfinished ticket is always some CTA's current tile, and its dependencies have smaller tickets,
@@ -194,6 +197,7 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
                 default: run_range_rare<2048>(sc, n0, sm, build); break;
             }
             tab_L = sc.L;
+            tab_N = 0;             // the range tile overwrites the row table
             __threadfence();       // this thread's S stores are visible device-wide ...
             __syncthreads();       // ... for every thread of the tile ...
             if (threadIdx.x == 0) atomicAdd(done + sg.scan, 1);   // ... before the tile is counted
@@ -214,8 +218,10 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
             __syncthreads();
             if (s_abort) break;
             if (sc.H) {
-                fft_row_tile(sc, local, sm, discard);
+                fft_row_tile(sc, local, sm, discard, tab_N != sc.n_az);
+                tab_N = sc.n_az;
             } else {
+                tab_N = 0;         // the gather tile overwrites the row table
                 const int r = local / sc.az_tiles_per_row;
                 const int th0 = (local - r * sc.az_tiles_per_row) * az::Geo<J>::TW;
                 az::azimuth_tile<J, true>(sc.S, sc.w, sc.o, sc.o_row_stride, sc.n_az, sc.K, sc.out, r, th0, sm, red);
