@@ -160,6 +160,9 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
     extern __shared__ __align__(16) char sm[];
     __shared__ int red[4 * az::THREADS / 32];
     __shared__ int s_ticket[2], s_abort;
+    // the segment and scan of the current and the next ticket, decoded once by the thread that takes the ticket
+    __shared__ Segment s_sg[2];
+    __shared__ ScanDev s_sc[2];
     int *head = counters + CNT_HEAD, *err = counters + CNT_ERR, *done = counters + CNT_DONE;
     const bool discard = (flags & ROSAR_BATCH_DISCARD_S) != 0;
     int tab_L = 0;   // L of the twiddle table left in shared memory by the previous range tile
@@ -169,19 +172,27 @@ batch_kernel(const ScanDev *__restrict__ scans, const Segment *__restrict__ segs
     // smallest unfinished ticket is always some CTA's current tile, and its dependencies have smaller tickets,
     // so every wait ends)
     constexpr int GRAB = 32;   // the thread that takes tickets (warp 1: thread 0 does the dependency waits)
-    if (threadIdx.x == GRAB) s_ticket[0] = atomicAdd(head, 1);
+    auto decode = [&](int slot, int tk) {     // the ticket's segment and scan into shared memory (GRAB only)
+        s_ticket[slot] = tk;
+        if (tk < total) {
+            const Segment g = segs[find_segment(segs, n_segs, tk)];
+            s_sg[slot] = g;
+            s_sc[slot] = scans[g.scan];
+        }
+    };
+    if (threadIdx.x == GRAB) decode(0, atomicAdd(head, 1));
     __syncthreads();
     for (int cur = 0;; cur ^= 1) {
         const int t = s_ticket[cur];
         if (t >= total) break;
-        const Segment sg = segs[find_segment(segs, n_segs, t)];
-        const ScanDev sc = scans[sg.scan];
+        const Segment sg = s_sg[cur];
+        const ScanDev &sc = s_sc[cur];
         const int local = t - sg.first + sg.start;
         if (threadIdx.x == 0) s_abort = 0;
         if (threadIdx.x == GRAB) {
             int nt = atomicAdd(head, 1);
             if (nt < total && ld_relaxed(err) != 0) nt = total;
-            s_ticket[cur ^ 1] = nt;
+            decode(cur ^ 1, nt);
         }
         if (sg.kind == 0) {
             const bool build = tab_L != sc.L;
