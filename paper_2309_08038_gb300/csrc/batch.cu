@@ -132,7 +132,7 @@ __device__ __forceinline__ void fft_row_tile(const ScanDev &sc, int r, char *sme
     const size_t row = (size_t)r * N;
     const float2 *Srow = sc.S + row;
     if (sc.fixed) {
-        __syncthreads();
+        if (build_tw) __syncthreads();        // else the caller's dependency barrier already ordered shared memory
         switch (sc.fixed) {                   // the run-time plan's radices, constant strides
             case 1: rowfft::row_filter_fused<1800, BT_THREADS, false, 8, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
             case 2: rowfft::row_filter_fused<3600, BT_THREADS, false, 16, 15, 15>(Srow, sc.H + row, 1.f, x, sc.out + row, tc, tf, discard); break;
