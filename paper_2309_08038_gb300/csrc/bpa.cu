@@ -45,10 +45,17 @@ __device__ __forceinline__ float2 read_bin(const float2 *__restrict__ S, int l, 
 }
 
 // Per chunk of offsets the bins a pixel of row r reads lie in a few rows near r (x = r + (R_n - rho)/dR, within a
-// couple of bins over a +-30 degree aperture): the rows [wlo, wlo + BPA_WR) around the chunk's nominal range of x
-// (one bin of margin each side) and the pulses th0 + dc .. th0 + dc + BPA_WC are staged in shared memory once, and
-// every (pixel, pulse) sample whose two bins fall in the window reads it there (others, e.g. under large supplied
-// position errors, read S through L2 as before).
+// couple of bins over a +-30 degree aperture): a window of rows around the chunk's range of x and the pulses
+// th0 + dc .. th0 + dc + BPA_WC are staged in shared memory once.  The range of x is the nominal one widened by
+// the largest distance a supplied pulse position lies from its nominal one: R_n is a distance from the pixel, so it
+// moves by at most |pos_n - pos_n,nominal| <= |dr_n| + 2*r0*|sin(eps_n/2)| (triangle inequality).  When that range,
+// with a bin of margin below and two above, fits the window (always with nominal geometry; with supplied errors
+// unless some pulse lies more than a bin or so off), every sample's bins are in it, rows outside [0, L) are staged
+// as zeros, and the pixel loop reads the window with no check.  Otherwise the window is the nominal one and each
+// sample whose bins fall outside it reads S through L2.
+// max that keeps a NaN (fmaxf drops it): a NaN error bound must reach the window test and fail it
+__device__ __forceinline__ float nanmax(float a, float b) { return (a > b || a != a) ? a : b; }
+
 // exp(-j*2*pi*q) for |q| up to 2^22 turns: q reduced by whole turns (q - rint(q), exact) to [-1/2, 1/2], then
 // the hardware sine and cosine of 2*pi times the remainder.
 __device__ __forceinline__ float2 expmj2pi_turns(float q) {
@@ -70,7 +77,7 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
     __shared__ float4 ptab[NOMINAL ? 1 : BPA_THREADS + BPA_DC];
     __shared__ float pal[NOMINAL ? 1 : BPA_THREADS + BPA_DC];
     __shared__ float2 rowph;
-    __shared__ float red_lo[BPA_THREADS / 32], red_hi[BPA_THREADS / 32];
+    __shared__ float red_lo[BPA_THREADS / 32], red_hi[BPA_THREADS / 32], red_e[BPA_THREADS / 32];
 
     const int r = blockIdx.y;
     const int th0 = blockIdx.x * BPA_THREADS;
@@ -125,6 +132,7 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                 dtab[i] = make_float4(s, c, x, 0.f);
             }
         }
+        float emax = 0.f;   // largest pulse position error of the chunk, in bins
         if (!NOMINAL) {
             for (int i = threadIdx.x; i < BPA_THREADS + nd; i += BPA_THREADS) {
                 const int n = pmod(th0 + dc + i, n_az);
@@ -135,61 +143,102 @@ bpa_kernel(const float2 *__restrict__ S, BpaParams p, const float *__restrict__ 
                 const float rn = r0 + drn;
                 ptab[i] = make_float4(ce, se, drn * (rn + r0 - 2.f * R), 4.f * R * rn);
                 pal[i] = rho - drn;
+                emax = nanmax(emax, fmaf(2.f * r0, fabsf(se), fabsf(drn)) * p.inv_dR);
             }
         }
-        // window rows from the chunk's nominal x range
+        // the chunk's x range and error bound over the CTA
 #pragma unroll
         for (int sft = 16; sft > 0; sft >>= 1) {
             xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, sft));
             xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, sft));
+            if (!NOMINAL) emax = nanmax(emax, __shfl_xor_sync(0xffffffffu, emax, sft));
         }
         if ((threadIdx.x & 31) == 0) {
             red_lo[threadIdx.x >> 5] = xlo;
             red_hi[threadIdx.x >> 5] = xhi;
+            red_e[threadIdx.x >> 5] = emax;
         }
         __syncthreads();
         xlo = red_lo[0];
         xhi = red_hi[0];
+        emax = red_e[0];
         for (int i = 1; i < BPA_THREADS / 32; ++i) {
             xlo = fminf(xlo, red_lo[i]);
             xhi = fmaxf(xhi, red_hi[i]);
+            if (!NOMINAL) emax = nanmax(emax, red_e[i]);
         }
-        const int wlo = max(0, (int)floorf(xlo) - 1);
-        const int whi = min(L - 1, (int)floorf(xhi) + 2);            // last staged row
-        const int nrow = min(BPA_WR, whi - wlo + 1);
+        // covered: every sample's x lies in [xlo - emax, xhi + emax] (up to rounding, far below the margins), so
+        // its bins floor(x) and floor(x) + 1 lie in rows [floor(xlo - emax) - 1, floor(xhi + emax) + 2]
+        const float flo = floorf(xlo - emax), fhi = floorf(xhi + emax);
+        const bool covered = fhi - flo <= (float)(BPA_WR - 4) && flo > -1e6f && fhi < 1e6f;   // false for NaN
+        int wlo, nrow;
+        if (covered) {
+            wlo = (int)flo - 1;
+            nrow = (int)(fhi - flo) + 4;
+        } else {
+            wlo = max(0, (int)floorf(xlo) - 1);
+            nrow = min(BPA_WR, min(L - 1, (int)floorf(xhi) + 2) - wlo + 1);
+        }
         const int wtop = wlo + nrow;                                  // rows [wlo, wtop) staged
         const int ncol = BPA_THREADS + nd;
         for (int e = threadIdx.x; e < nrow * ncol; e += BPA_THREADS) {
             const int rr = e / ncol, cc = e - rr * ncol;
             const int n = pmod(th0 + dc + cc, n_az);
-            wsm[rr * BPA_WC + cc] = __ldg(S + (size_t)(wlo + rr) * n_az + n);
+            const int l = wlo + rr;
+            wsm[rr * BPA_WC + cc] = (l >= 0 && l < L) ? __ldg(S + (size_t)l * n_az + n) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        if (th < n_az) {
+        if (th >= n_az) continue;
+        // bin x and weight alpha * exp(-j*2*pi*(2 f/c)*delta) of offset dc + i for this thread's pixel
+        auto sample = [&](int i, float &x, float2 &a) {
+            const float4 t = dtab[i];
+            if (NOMINAL) {
+                x = t.x;
+                a = make_float2(t.y, t.z);
+            } else {
+                const float4 pp = ptab[threadIdx.x + i];
+                const float sh = fmaf(t.x, pp.x, t.y * pp.y);            // sin((pi*d/n_az) + eps/2)
+                const float s2 = sh * sh;
+                const float num = fmaf(pp.w, s2, pp.z);                  // R_n^2 - rho^2
+                const float Rn2 = fmaf(rho, rho, num);
+                // branch-free: R_n = 0 (the facing pulse of row 0, or a supplied position on the pixel) gives
+                // delta = num / rho = -rho exactly, or 0 when rho = 0 too, and alpha = 1 by the select
+                const float inv = rsqrtf(fmaxf(Rn2, 1e-30f));
+                const float Rn = Rn2 * inv;
+                const float delta = __fdividef(num, fmaxf(Rn + rho, 1e-30f));
+                // alpha = max(0, cos(theta')), cos(theta') <= 1: one saturating multiply
+                const float a0 = __saturatef(fmaf(-2.f * R, s2, pal[threadIdx.x + i]) * inv);
+                const float alpha = Rn2 > 0.f ? a0 : 1.f;
+                x = fmaf(delta, p.inv_dR, rf);
+                a = cscale(expmj2pi_turns(p.two_f_over_c * delta), alpha);
+            }
+        };
+        if (covered) {
+            // in-window by construction; the unsigned clamp keeps even a NaN x's read inside the staged rows
+            const float2 *colp = wsm + threadIdx.x;
 #pragma unroll 4
             for (int i = 0; i < nd; ++i) {
-                const float4 t = dtab[i];
                 float x;
                 float2 a;
-                if (NOMINAL) {
-                    x = t.x;
-                    a = make_float2(t.y, t.z);
+                sample(i, x, a);
+                float2 sv;
+                if (LINEAR) {
+                    const float fl = floorf(x);
+                    const unsigned rel = min((unsigned)(int)fl - (unsigned)wlo, (unsigned)(nrow - 2));
+                    const float2 s0 = colp[rel * BPA_WC + i], s1 = colp[(rel + 1) * BPA_WC + i];
+                    sv = caxpy(x - fl, csub(s1, s0), s0);
                 } else {
-                    const float4 pp = ptab[threadIdx.x + i];
-                    const float sh = fmaf(t.x, pp.x, t.y * pp.y);            // sin((pi*d/n_az) + eps/2)
-                    const float s2 = sh * sh;
-                    const float num = fmaf(pp.w, s2, pp.z);                  // R_n^2 - rho^2
-                    const float Rn2 = fmaf(rho, rho, num);
-                    // branch-free: R_n = 0 (the facing pulse of row 0, or a supplied position on the pixel) gives
-                    // delta = num / rho = -rho exactly, or 0 when rho = 0 too, and alpha = 1 by the select
-                    const float inv = rsqrtf(fmaxf(Rn2, 1e-30f));
-                    const float Rn = Rn2 * inv;
-                    const float delta = __fdividef(num, fmaxf(Rn + rho, 1e-30f));
-                    const float a0 = fmaxf(0.f, fmaf(-2.f * R, s2, pal[threadIdx.x + i]) * inv);
-                    const float alpha = Rn2 > 0.f ? a0 : 1.f;
-                    x = fmaf(delta, p.inv_dR, rf);
-                    a = cscale(expmj2pi_turns(p.two_f_over_c * delta), alpha);
+                    const unsigned rel = min((unsigned)(int)floorf(x + 0.5f) - (unsigned)wlo, (unsigned)(nrow - 1));
+                    sv = colp[rel * BPA_WC + i];
                 }
+                cmac(acc, a, sv);
+            }
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < nd; ++i) {
+                float x;
+                float2 a;
+                sample(i, x, a);
                 const int col = threadIdx.x + i;
                 float2 sv;
                 if (LINEAR) {

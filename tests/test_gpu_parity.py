@@ -257,6 +257,54 @@ def test_bpa_with_pulse_errors_matches_oracle(rosar, torch):
         assert rel_l2(got[r], ref) < TOL_IMAGE, r
 
 
+@pytest.mark.parametrize("interp", ["linear", "nearest"])
+def test_bpa_large_pulse_errors_mixed_windows(rosar, torch, interp):
+    """Supplied positions several range bins off on a few pulses (Eq. (37)): the azimuth tile whose pulses include
+    them (pixels 0..255 read pulses -30..285; pixels 256..359 read 226..359 and 0..180, so pulses 190..199 are
+    the first tile's alone) cannot bound its bins by the staged window and reads those samples through L2, the
+    other tile reads the window unchecked.  With a moderate error everywhere nearly every window is bounded (the
+    first rows, where x spans most bins, are not)."""
+    cfg = synth.TINY
+    rng = np.random.default_rng(21)
+    S = crand(rng, cfg.L, cfg.n_az)
+    rad = oracle_radar(cfg)
+    dR = O.range_bin_spacing(rad, cfg.L)
+    for big in (True, False):
+        dr = (0.3 * dR * rng.uniform(-1, 1, cfg.n_az)).astype(np.float32)
+        dphi = np.deg2rad(0.2 * rng.uniform(-1, 1, cfg.n_az)).astype(np.float32)
+        if big:        # pulses 190..199: 3.5 bins out and 4 degrees off
+            dr[190:200] = np.float32(3.5 * dR)
+            dphi[190:200] = np.float32(np.deg2rad(4.0))
+        got = host(rosar.bpa(dev(torch, S), api_radar(rosar, cfg), cfg.L, cfg.M_ap, interp=interp,
+                             dphi=dev(torch, dphi), dr=dev(torch, dr)))
+        rows = np.arange(cfg.L)
+        ref = np.stack([O.bpa_pixels(S, rad, cfg.n_az, cfg.M_ap, np.full(cfg.n_az, r), np.arange(cfg.n_az),
+                                     interp=interp, dphi=dphi.astype(np.float64), dr=dr.astype(np.float64))
+                        for r in rows])
+        if interp == "nearest":      # rounding at a bin's midpoint may pick either bin: compare the pixels
+            # whose every sample lies clear of a midpoint in the oracle's own geometry
+            keep = _clear_of_midpoints(rad, cfg, dR, dphi, dr)
+            assert keep.mean() > 0.3
+            assert rel_l2(got[keep], ref[keep]) < TOL_IMAGE, big
+        else:
+            assert rel_l2(got, ref) < TOL_IMAGE, big
+
+
+def _clear_of_midpoints(rad, cfg, dR, dphi, dr):
+    """Pixels of the tiny grid whose every (pixel, pulse) bin position lies more than 1e-3 of a bin from a
+    midpoint between bins (nearest-bin reads agree there whatever the float rounding)."""
+    M = cfg.M_ap
+    d = np.arange(-(M // 2), M - M // 2)
+    keep = np.zeros((cfg.L, cfg.n_az), dtype=bool)
+    th = np.arange(cfg.n_az)
+    n = (th[:, None] + d[None, :]) % cfg.n_az
+    phi_n = O.phase_centre_angle(d, cfg.n_az)[None, :] + dphi.astype(np.float64)[n]
+    for r in range(cfg.L):
+        x = O.slant_range(rad.r0 + r * dR, 0.0, rad.r0 + dr.astype(np.float64)[n], phi_n) / dR
+        keep[r] = np.all(np.abs(x - np.floor(x) - 0.5) > 1e-3, axis=1)
+    return keep
+
+
 def test_bpa_row_subset_and_ragged_azimuth(rosar, torch):
     rng = np.random.default_rng(9)
     cfg = synth.TINY
