@@ -25,7 +25,8 @@
 // sincospif's software range reduction and polynomials: the per-sample work is issue-bound FP32 and SFU.
 // The interpolation mode is a template parameter.
 //
-// Grid: (azimuth tiles of 256 pixels, rows).  Compute-bound (FP32 + SFU) once S is staged in shared memory.
+// Grid: (azimuth tiles of 256 pixels, rows).  Once S is staged in shared memory the nominal kernel is bound by
+// shared-memory bandwidth (two 8-byte window reads per sample) and the supplied-error kernel by FP32 + SFU issue.
 
 #include "rosar_internal.cuh"
 
