@@ -247,7 +247,9 @@ ROSAR_API rosar_status rosar_sas_time(const rosar_c32 *raw, const float *win, co
  *     arguments as rosar_sas_time (shared offsets o [K], any int32 values) / rosar_bpa_time.
  *   rosar_sas_time_planned / rosar_bpa_time_planned: the image from raw [n_az][L] (device, 16-byte aligned)
  *     with the plan (read only; n_az, L, n_rng and K as given to the plan call).  Limits as the unplanned
- *     calls, and ceil(n_rng / 64) <= 65535, K <= 65535.
+ *     calls, and ceil(n_rng / 64) <= 65535, K <= 65535.  The call cannot check a plan's contents or size: a
+ *     plan not written by the matching plan call with these sizes gives an undefined image and may read past
+ *     the plan's end (the caller owns the plan and keeps it alive until the call's stream has passed it).
  */
 ROSAR_API size_t rosar_time_domain_plan_bytes(int n_rng, int L, int K);
 ROSAR_API rosar_status rosar_sas_time_plan(const float *win, const rosar_c32 *w, const int32_t *o,
