@@ -213,6 +213,36 @@ def test_nearest_bpa_equals_full_aperture_matched_filter():
     assert checked == 3
 
 
+@pytest.mark.parametrize("errors", [False, True])
+def test_linear_bpa_is_exact_on_range_profiles_affine_in_the_bin(errors):
+    """Linear interpolation between bins floor(x) and floor(x) + 1 reproduces a range profile that is affine in
+    the bin index exactly, so with S[l, n] = (a + b*l) c_n the BPA sum has the closed form
+    sum_d alpha_d exp(-j 2 k_mid R_d) (a + b R_d / dR) c_n (Sec. III-D with w_BP), at nominal and at supplied
+    pulse positions (Eq. (37)).  Swapped interpolation weights, an off-by-one bin or a dropped term fail it."""
+    L, n_az, M = 64, 360, 24
+    rad = _radar77(L)
+    dR = O.range_bin_spacing(rad, L)
+    k_mid = O.wavenumber_centred(rad, L)
+    rng = np.random.default_rng(11)
+    a, b = complex(rng.standard_normal(), rng.standard_normal()), complex(rng.standard_normal(), 0.3)
+    c = rng.standard_normal(n_az) + 1j * rng.standard_normal(n_az)
+    S = (a + b * np.arange(L))[:, None] * c[None, :]
+    dphi = rng.uniform(-1, 1, n_az) * math.radians(0.5) if errors else None
+    dr = rng.uniform(-1, 1, n_az) * 0.4 * dR if errors else None
+    d = np.arange(-(M // 2), M - M // 2)
+    for r, th in ((10, 0), (25, 123), (50, 359)):
+        R = rad.r0 + r * dR
+        n = (th + d) % n_az
+        phi_rel = O.phase_centre_angle(d, n_az) + (dphi[n] if errors else 0.0)
+        r_n = rad.r0 + (dr[n] if errors else 0.0)
+        R_d = O.slant_range(R, 0.0, r_n, phi_rel)
+        assert np.all((R_d / dR >= 0) & (R_d / dR < L - 1))          # every sample inside the profile
+        alpha = O.antenna_pattern(O.off_boresight_angle(R, 0.0, r_n, phi_rel))
+        ref = np.sum(alpha * np.exp(-2j * k_mid * R_d) * (a + b * R_d / dR) * c[n])
+        got = O.bpa_pixels(S, rad, n_az, M, [r], [th], interp="linear", dphi=dphi, dr=dr)[0]
+        assert abs(got - ref) <= 1e-11 * np.sum(np.abs(alpha * (a + b * R_d / dR) * c[n]))
+
+
 def test_bpa_uses_the_supplied_pulse_positions():
     """With rotation errors (Eq. (37)) in the data, BPA given the true positions recovers the
     error-free peak; BPA on nominal positions loses coherence."""
