@@ -243,6 +243,30 @@ def test_linear_bpa_is_exact_on_range_profiles_affine_in_the_bin(errors):
         assert abs(got - ref) <= 1e-11 * np.sum(np.abs(alpha * (a + b * R_d / dR) * c[n]))
 
 
+def test_pulse_position_error_bounds_the_slant_range_change():
+    """The GPU BPA sizes its staged range window with this bound: moving a phase centre from (r0, phi) to
+    (r0 + dr, phi + eps) changes its distance to any pixel (Eq. (2)) by at most |dr| + 2 r0 |sin(eps/2)|
+    (triangle inequality), with equality for a pixel on the line through the two positions."""
+    rng = np.random.default_rng(12)
+    r0 = 0.25
+    R = r0 + rng.uniform(0.0, 15.0, 20000)
+    phi_t = rng.uniform(-math.pi, math.pi, R.shape)
+    phi = rng.uniform(-math.pi, math.pi, R.shape)
+    eps = rng.normal(0.0, math.radians(2.0), R.shape)
+    dr = rng.normal(0.0, 0.01, R.shape)
+    change = np.abs(O.slant_range(R, phi_t, r0 + dr, phi + eps) - O.slant_range(R, phi_t, r0, phi))
+    bound = np.abs(dr) + 2.0 * r0 * np.abs(np.sin(eps / 2.0))
+    assert np.all(change <= bound * (1 + 1e-12) + 1e-15)
+    # tight: a radial move seen from a pixel beyond it on the same ray, and a rotation by eps seen from a pixel
+    # on the extension of the chord between the two positions
+    assert abs(O.slant_range(3.0, 0.0, r0 + 0.02, 0.0) - O.slant_range(3.0, 0.0, r0, 0.0)) == pytest.approx(0.02)
+    e = 0.3
+    p0, p1 = r0, r0 * complex(math.cos(e), math.sin(e))
+    x = p1 + 2.0 * (p1 - p0) / abs(p1 - p0)
+    d = O.slant_range(abs(x), math.atan2(x.imag, x.real), r0, 0.0) - O.slant_range(abs(x), math.atan2(x.imag, x.real), r0, e)
+    assert d == pytest.approx(2.0 * r0 * math.sin(e / 2.0), rel=1e-12)
+
+
 def test_bpa_uses_the_supplied_pulse_positions():
     """With rotation errors (Eq. (37)) in the data, BPA given the true positions recovers the
     error-free peak; BPA on nominal positions loses coherence."""
